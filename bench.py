@@ -1,0 +1,352 @@
+"""Benchmark: time to solve the 128^3 lognormal-diffusivity Poisson system
+(random + RCM ordering) to relative residual 1e-8 on one GB300.
+
+A step is one complete solve through the C ABI (repacked matrix resident in
+HBM, right-hand side resident): the mixed-precision pipelined PCG (float
+recurrences, FP64 solution and residual replacement) is the headline; plain
+FP64 Jacobi-PCG and FP64 pipelined PCG are timed the same way beside it.
+Every step starts with an L2 flush (a 256 MB write, outside the timed
+events); each step is timed with CUDA events on the solve's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--size S] [--skip-fp64]
+
+--impl reference times the oracle (plain C, FP64 Jacobi-PCG, one host core)
+on a bounded sample of the same workload and scales it to a full solve.
+Under torchrun (N > 1) every rank solves its own replica (no data exchange:
+the single-system solve is not partitioned here) and rank 0 prints the
+maximum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "128³ Poisson solve to 1e-8 rel. res.: s and HBM GB/s, mixed vs FP64 PCG"
+TOL = 1e-8
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---- algorithmic bytes (one launch = one solve) ------------------------------
+# Per cell, with f = 2F/n off-diagonal entries per row (actual, padding
+# excluded), float values/indices 4 B, double 8 B; vectors counted once per
+# pass they are read or written, gathers once.
+def bytes_mixed(n, F, iters, reps):
+    f = 2.0 * F / n
+    loop = f * 8 + 6 * 4 + 6 * 4                  # matrix (val32+col) + 6 reads + 6 writes
+    rep = (24                                     # fold: xhat rw, xc rw
+           + f * 12 + 8 + 8 + 8 + 8 + 4           # FP64 residual: val64+col, xhat, bhat, dg, r out
+           + f * 8 + 4 + 4 + 4 + 4                # w = Ar, s = Ap
+           + f * 8 + 4 + 4 + 8 + 8 + 4)           # z = As, rescale r, p, read w
+    ends = 8 * 4 + 4 * 4 + 3 * 8                  # prep (b, x0 in; bhat, xhat out; zero 4 float) + unscale
+    return n * (iters * loop + reps * rep + ends)
+
+
+def bytes_pcg64(n, F, iters, reps):
+    f = 2.0 * F / n
+    spmv = f * 12 + 8 + 8                         # q = A p: val64+col, p, q out
+    upd = 5 * 8 + 2 * 8                           # x, p, r, q, dg in; x, r out
+    pup = 3 * 8                                   # p = r + beta p
+    res = f * 12 + 8 + 8 + 8 + 8                  # true residual
+    return n * (iters * (spmv + upd + pup) + reps * res + 6 * 8)
+
+
+def bytes_pipe64(n, F, iters, reps):
+    f = 2.0 * F / n
+    loop = f * 12 + 7 * 8 + 6 * 8                 # matrix + w,z,s,p,x,r,dg in; 6 out
+    rep = (f * 12 + 4 * 8 + 8) + (f * 12 + 2 * 8 + 2 * 8) + (f * 12 + 4 * 8 + 8)
+    return n * (iters * loop + reps * rep + 8 * 8)
+
+
+# ---- clocks ----------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---- the oracle arm --------------------------------------------------------
+def oracle_sample(sys_, iters_cap):
+    """Seconds per FP64 PCG iteration of the oracle over a capped run."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.pcg(sys_, tol=TOL, maxit=iters_cap)
+    dt = time.perf_counter() - t0
+    return dt / max(r.iters, 1), r
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import ldu_cases as lc
+    import oracle
+    s = lc.config2(s=args.size, seed=0)
+    oracle.lib()
+    full = oracle.pcg(s, tol=TOL)              # iteration count of the full solve
+    cap = args.ref_iters
+    for _ in range(args.warmup):
+        oracle_sample(s, cap)
+    per = []
+    for _ in range(args.steps):
+        t_it, _ = oracle_sample(s, cap)
+        per.append(t_it * full.iters)
+    value = statistics.mean(per)
+    sample = (f"{cap} FP64 Jacobi-PCG iterations of the {args.size}^3 case per step, scaled to "
+              f"the oracle's full {full.iters}-iteration solve")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"poisson {args.size}^3 lognormal(0,1) k, random+RCM order, "
+                               "Jacobi-PCG to 1e-8 (oracle, plain C)", "cells": s.n,
+                   "faces": s.nfaces},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_iters": full.iters, "oracle_relres": full.relres,
+    }
+    print(json.dumps(line))
+
+
+# ---- our arm ---------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import ldu_cases as lc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1505_07630_gb300 as pkg
+
+    s = lc.config2(s=args.size, seed=0)
+    n, F = s.n, s.nfaces
+    A = pkg.from_system(s, device=dev, slice_rows=args.slice_rows, block_threads=args.block_threads)
+    b = torch.as_tensor(s.b, device=dev)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(call, steps, warmup):
+        for _ in range(warmup):
+            x.zero_()
+            call()
+        torch.cuda.synchronize(dev)
+        times, outs = [], []
+        for _ in range(steps):
+            x.zero_()
+            flush.fill_(1.0)                       # evict the previous step from L2
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = call()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+            outs.append(out)
+        return times, outs
+
+    def mixed():
+        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="mixed",
+                                         rr_period=args.rr_period)
+        return st, it, rr, A.stats()["replacements"]
+
+    def pcg64():
+        _, st, it, rr = pkg.pcg_solve(A, b, x, tol=TOL)
+        return st, it, rr, A.stats()["replacements"]
+
+    def pipe64():
+        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="fp64")
+        return st, it, rr, A.stats()["replacements"]
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_mixed, o_mixed = timed(mixed, args.steps, args.warmup)
+    x_mixed = x.cpu().numpy()
+    if dist is not None:
+        tt = torch.tensor([sum(t_mixed)], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt)
+    else:
+        total = sum(t_mixed)
+    st, it, rr, reps = o_mixed[-1]
+    grid = A.stats()
+    step_s = total / args.steps
+    hbm, peak_kind = peaks()
+    alg_bytes = bytes_mixed(n, F, it, reps)
+    achieved = alg_bytes / statistics.median(t_mixed) / 1e9
+
+    extra = {}
+    if not args.skip_fp64:
+        t_pcg, o_pcg = timed(pcg64, max(2, args.steps // 2), 1)
+        t_pipe, o_pipe = timed(pipe64, max(2, args.steps // 2), 1)
+        pst, pit, prr, preps = o_pcg[-1]
+        qst, qit, qrr, qreps = o_pipe[-1]
+        mp = statistics.median(t_pcg)
+        mq = statistics.median(t_pipe)
+        extra = {
+            "fp64_pcg": {"s": mp, "iters": pit, "relres": prr, "status": pst,
+                         "alg_gbs": bytes_pcg64(n, F, pit, preps) / mp / 1e9},
+            "fp64_pipecg": {"s": mq, "iters": qit, "relres": qrr, "status": qst,
+                            "alg_gbs": bytes_pipe64(n, F, qit, qreps) / mq / 1e9},
+            "speedup_mixed_vs_fp64_pcg": mp / statistics.median(t_mixed),
+        }
+
+    # end to end through the public API: pinned host b in, solve, x back to pinned host
+    hb = torch.empty(n, dtype=torch.float64).pin_memory()
+    hb.copy_(torch.as_tensor(s.b))
+    hx = torch.empty(n, dtype=torch.float64).pin_memory()
+    bd = torch.empty(n, dtype=torch.float64, device=dev)
+
+    def e2e_step():
+        bd.copy_(hb, non_blocking=True)
+        x.zero_()
+        pkg.pipecg_solve(A, bd, x, tol=TOL, precision="mixed", rr_period=args.rr_period)
+        hx.copy_(x, non_blocking=True)
+        return None
+
+    t_e2e, _ = timed(e2e_step, args.steps, 1)
+    e2e_s = statistics.mean(t_e2e)
+
+    # CPU baseline: the oracle on this host, bounded sample, rank 0 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        full_iters = extra.get("fp64_pcg", {}).get("iters", it)
+        t_it, _ = oracle_sample(s, args.ref_iters)
+        cpu = {"value": t_it * full_iters, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.ref_iters} FP64 Jacobi-PCG iterations of the {args.size}^3 case "
+                         f"(plain C oracle, one core), scaled to {full_iters} iterations"}
+
+    relres_oracle = None
+    if rank == 0:
+        import oracle
+        relres_oracle = oracle.true_relres(s, x_mixed)
+
+    line = {
+        "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"poisson {args.size}^3 lognormal(0,1) k, harmonic faces, random+RCM "
+                               "order, Dirichlet x-walls; mixed pipelined Jacobi-PCG to 1e-8",
+                   "cells": n, "faces": F, "slice_rows": A.info()["slice_rows"],
+                   "grid_blocks": grid["grid_blocks"], "block_threads": grid["block_threads"],
+                   "rr_period": args.rr_period, "l2": "256 MB flush before every step",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "solve": {"status": st, "iters": it, "replacements": reps, "relres": rr,
+                  "relres_oracle": relres_oracle},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_mixed (persistent, one launch per solve)",
+                     "alg_bytes_per_launch": alg_bytes},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line))
+    A.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=128)
+    ap.add_argument("--slice-rows", type=int, default=0)
+    ap.add_argument("--block-threads", type=int, default=0)
+    ap.add_argument("--rr-period", type=int, default=16)
+    ap.add_argument("--ref-iters", type=int, default=60)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        ap.error("need steps >= 1")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

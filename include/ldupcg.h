@@ -1,0 +1,209 @@
+/*
+ * ldupcg.h -- C interface of libldupcg: Jacobi-preconditioned conjugate
+ * gradients, plain and pipelined, for symmetric finite-volume systems stored
+ * in OpenFOAM LDU face addressing, on one GB300 GPU (sm_103a).
+ *
+ * The operation (Sec. 2, Eq. 9): solve A x = b, A square, symmetric and
+ * positive definite, one row per mesh cell.  A arrives in the lduMatrix
+ * layout the paper names (Sec. 5): diag[n]; for each internal face f an
+ * owner cell owner[f] and a neighbour cell neighbour[f] with owner < neighbour,
+ * upper[f] = A[owner, neighbour] and lower[f] = A[neighbour, owner].  The
+ * number of non-zeros is n + 2*nFaces (Sec. 4.2, the n_i + 2 o_i of Eq. 2).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named in the argument list as "device" must point to memory of
+ *    the GPU that was current when the matrix handle was created; "host"
+ *    pointers to ordinary host memory.  The caller owns every buffer it
+ *    passes; the library keeps no pointer to caller memory after a call
+ *    returns.  A handle owns its own device allocations (repacked matrix,
+ *    work vectors) until ldu_destroy.
+ *  - Work is queued on `stream` (a cudaStream_t; NULL = the legacy default
+ *    stream).  Entry points that return host results (iteration counts,
+ *    residuals, statuses) synchronise that stream before returning; the
+ *    others return once the work is queued.
+ *  - The return value is a status (ldu_status).  0 is success, 1 means the
+ *    iteration cap was reached (outputs hold the last iterate), negative
+ *    values are errors; no C++ exception crosses this interface.  On an
+ *    error, outputs are unspecified but buffers stay valid.
+ *  - A handle must not be used by two calls that may run concurrently: the
+ *    solves of one handle share its work vectors.
+ */
+#ifndef LDUPCG_H
+#define LDUPCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ldu_matrix ldu_matrix;       /* opaque handle */
+typedef struct CUstream_st *ldu_stream_t;   /* identical to cudaStream_t */
+
+typedef enum ldu_status {
+    LDU_OK = 0,
+    LDU_NOT_CONVERGED = 1,          /* iteration cap reached */
+    LDU_ERR_BAD_ARG = -1,           /* null pointer, negative size, bad option */
+    LDU_ERR_BAD_ADDRESSING = -2,    /* owner >= neighbour or an index outside [0, n) */
+    LDU_ERR_NOT_SPD = -3,           /* non-positive diagonal or CG breakdown (p^T A p <= 0) */
+    LDU_ERR_CUDA = -4,              /* a CUDA runtime call failed */
+    LDU_ERR_BARRIER_TIMEOUT = -5,   /* a grid barrier of a persistent kernel timed out */
+    LDU_ERR_OOM = -6,               /* device allocation failed */
+    LDU_ERR_UNSUPPORTED = -7        /* size beyond what the layout can index */
+} ldu_status;
+
+typedef enum ldu_precision {
+    LDU_FP64 = 0,      /* everything in double */
+    LDU_FP32 = 1,      /* ldu_spmv only: float values and vectors */
+    LDU_MIXED = 2      /* float pipelined recurrences, double residual and solution */
+} ldu_precision;
+
+/* Layout options of the repacked matrix and launch shape of its kernels.
+ * A zeroed struct (or NULL) selects the defaults. */
+typedef struct ldu_opts {
+    int slice_rows;     /* rows per sliced-ELL slice: 32, 64 or 128 (default 128) */
+    int block_threads;  /* threads per block of the persistent solve kernels:
+                           128 or 256 (default 256) */
+    int blocks_per_sm;  /* resident blocks per SM for the persistent kernels;
+                           0 = as many as fit */
+} ldu_opts;
+
+/* Options of pipecg_solve (and pcg_solve_batched).  NULL or zeroed selects
+ * the defaults given here. */
+typedef struct pcg_opts {
+    int rr_period;          /* iterations between residual replacements:
+                               LDU_FP64 default 0 (replace only when the
+                               recursive residual reaches tol);
+                               LDU_MIXED default 16 (FP64 replacement) */
+    double tau;             /* LDU_MIXED: also replace when (r, M^-1 r) has
+                               dropped by tau^2 since the last replacement;
+                               0 = off (default) */
+    int restart;            /* LDU_MIXED: 1 = every replacement restarts the
+                               search (classic defect correction with inner
+                               tolerance tau); 0 = keep the search directions
+                               (default) */
+    double barrier_timeout_s;  /* grid-barrier spin limit, default 10 s */
+    int fault_inject;       /* testing only: 1 = block 0 of the persistent kernel
+                               returns before its first barrier, so the others
+                               time out and the call returns
+                               LDU_ERR_BARRIER_TIMEOUT; 0 otherwise */
+} pcg_opts;
+
+/* Counters of the last solve on a handle. */
+typedef struct ldu_solve_stats {
+    int status;
+    int iters;              /* A*p products of the loop (float ones for LDU_MIXED) */
+    int replacements;       /* true-residual evaluations, initial one included */
+    double relres;          /* ||b - A x||_2 / ||b||_2 at exit, in FP64 */
+    double bnorm;           /* ||b||_2 */
+    int grid_blocks;        /* blocks of the persistent launch */
+    int block_threads;
+} ldu_solve_stats;
+
+/* Facts about a handle's device layout. */
+typedef struct ldu_info {
+    int64_t n, n_faces;
+    int64_t n_padded;       /* rows rounded up to whole slices */
+    int64_t nnz_padded;     /* stored off-diagonal slots incl. padding */
+    int slice_rows;
+    int64_t n_slices;
+    int max_row_entries;    /* widest slice */
+    int64_t device_bytes;   /* bytes the handle holds on the device */
+} ldu_info;
+
+/* Create a handle from an LDU matrix (Sec. 5, lduMatrix; Eq. 9's A).
+ *   n, nFaces           cells and internal faces (n >= 0, nFaces >= 0)
+ *   owner, neighbour    device int32[nFaces]: owner[f] < neighbour[f], both in [0, n);
+ *                       faces need not be sorted
+ *   diag                device double[n], every entry > 0
+ *   upper, lower        device double[nFaces]
+ *   opt                 host, may be NULL
+ *   out                 host: receives the handle (NULL on failure)
+ * Validates the addressing on the device, repacks A into the handle's
+ * sliced-ELL layout (rows in the caller's order, off-diagonals of a row in
+ * ascending column order, symmetric diagonal scaling applied) and keeps a
+ * copy of owner/neighbour for ldu_face_grad.  Synchronises `stream`.
+ * Errors: BAD_ARG, BAD_ADDRESSING, NOT_SPD (diag <= 0 or not finite), OOM,
+ * UNSUPPORTED (n or the padded non-zero count above 2^31 - 1), CUDA. */
+int ldu_create(int64_t n, int64_t nFaces, const int32_t *owner, const int32_t *neighbour,
+               const double *diag, const double *upper, const double *lower,
+               const ldu_opts *opt, ldu_stream_t stream, ldu_matrix **out);
+
+/* Replace the values of a handle's matrix, keeping its addressing
+ * (device double diag[n], upper[nFaces], lower[nFaces]).  Queued on stream;
+ * a non-positive diagonal is reported by the next solve as NOT_SPD. */
+int ldu_update_values(ldu_matrix *A, const double *diag, const double *upper,
+                      const double *lower, ldu_stream_t stream);
+
+/* Set the matrix of a finite-volume Laplacian from face coefficients:
+ * upper = lower = -coef[f], diag[i] = diag_extra[i] + sum of coef over the
+ * faces of cell i (the positive assembly of Sec. 2, Eq. 8's operator).
+ *   coef        device double[nFaces]
+ *   diag_extra  device double[n]: boundary-condition part of the diagonal
+ * The row sums are formed in a fixed order, so repeated calls agree bitwise. */
+int ldu_set_face_coeffs(ldu_matrix *A, const double *coef, const double *diag_extra,
+                        ldu_stream_t stream);
+
+/* y = A x (Sec. 2.1's sparse matrix-vector product; Table 1's first kernel).
+ *   precision  LDU_FP64: x, y are device double[n], values in double;
+ *              LDU_FP32: x, y are device float[n], values and sums in float.
+ * Queued on stream. */
+int ldu_spmv(const ldu_matrix *A, int precision, const void *x, void *y, ldu_stream_t stream);
+
+/* Jacobi-preconditioned CG (Sec. 2, Eq. 9; Saad, Iterative Methods, Alg. 9.1
+ * with M = diag(A)), FP64, one persistent cooperative launch with three grid
+ * barriers per iteration.
+ *   b        device double[n]
+ *   x        device double[n]: initial guess in, solution out
+ *   tol      stop when the recursive ||r||_2/||b||_2 <= tol and the true
+ *            residual recomputed at that point confirms it (else the search
+ *            restarts from the true residual)
+ *   maxit    cap on iterations (>= 0)
+ *   iters    host, may be NULL: iterations taken
+ *   relres   host, may be NULL: true ||b - A x||_2/||b||_2 at exit
+ * b = 0 gives x = 0, relres = 0.  Synchronises stream.
+ * Returns OK, NOT_CONVERGED, NOT_SPD (breakdown), BARRIER_TIMEOUT, BAD_ARG, CUDA. */
+int pcg_solve(const ldu_matrix *A, const double *b, double *x, double tol, int maxit,
+              int *iters, double *relres, ldu_stream_t stream);
+
+/* Pipelined Jacobi-PCG (Sec. 4.1; Ghysels and Vanroose 2014): one grid-level
+ * reduction per iteration, overlapped with the matrix-vector product.
+ *   precision  LDU_FP64: the recurrences in double, residual replacement when
+ *              the recursive residual reaches tol (and every rr_period steps);
+ *              LDU_MIXED: the recurrences in float on a float copy of the
+ *              matrix; the solution accumulates in double and the residual
+ *              is replaced by the double b - A x every rr_period steps.
+ *   opts       host, may be NULL
+ * Other arguments as pcg_solve.  A non-positive pipelined denominator is
+ * treated as rounding drift (replace and restart); only a non-positive
+ * (A u, u) on a fresh start returns NOT_SPD. */
+int pipecg_solve(const ldu_matrix *A, const double *b, double *x, double tol, int maxit,
+                 int precision, const pcg_opts *opts, int *iters, double *relres,
+                 ldu_stream_t stream);
+
+/* Gradient of a loss with respect to the face coefficients of
+ * ldu_set_face_coeffs, given the adjoint solution lambda = A^-T dL/dx and
+ * the forward solution x:  dcoef[f] = -(lambda[o] - lambda[n]) (x[o] - x[n])
+ * with o = owner[f], n = neighbour[f] (device double arrays; dcoef has
+ * nFaces entries in the caller's face order).  Queued on stream. */
+int ldu_face_grad(const ldu_matrix *A, const double *lambda, const double *x, double *dcoef,
+                  ldu_stream_t stream);
+
+/* Counters of the last solve (host struct filled from host memory; no sync). */
+int ldu_last_stats(const ldu_matrix *A, ldu_solve_stats *stats);
+
+/* Layout facts of a handle. */
+int ldu_get_info(const ldu_matrix *A, ldu_info *info);
+
+/* Free a handle and everything it owns (NULL is ignored).  Waits for the
+ * device work queued on the handle's kernels to finish. */
+void ldu_destroy(ldu_matrix *A);
+
+/* A static string naming a status code. */
+const char *ldu_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDUPCG_H */

@@ -1,0 +1,9 @@
+"""GB300-native Jacobi / pipelined PCG for OpenFOAM-style LDU matrices.
+
+The compute path is libldupcg (hand-written sm_103a CUDA behind a C ABI,
+include/ldupcg.h); this package holds its build script, the ctypes binding
+and the autograd wrapper.  PyTorch supplies device memory and streams only.
+"""
+from .ldupcg import (LduError, LduMatrix, from_system, ldu_create, ldu_destroy,  # noqa: F401
+                     ldu_face_grad, ldu_set_face_coeffs, ldu_spmv, ldu_update_values, lib,
+                     library_path, pcg_solve, pipecg_solve, status_string)

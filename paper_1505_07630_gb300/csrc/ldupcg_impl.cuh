@@ -1,0 +1,413 @@
+// ldupcg_impl.cuh -- internal types and device helpers of libldupcg.
+//
+// Device layout of a handle (all arrays padded to n_pad = n_slices * C rows):
+//   sliced ELL (SELL-C, sigma = 1): slice s holds rows [s*C, s*C + C); its
+//   width w_s is the longest off-diagonal row in it; entry k of row
+//   s*C + i sits at slice_ptr[s] + k*C + i ("column-major in the slice"), so
+//   a warp reads C consecutive values per k.  A lane owns R = C/32
+//   consecutive rows and reads them with one R-wide vector load.  Padding
+//   slots hold col = own row, value 0.
+//   Values are stored symmetrically scaled, Ahat = D^-1/2 A D^-1/2 (unit
+//   diagonal, not stored), in double (val64) and float (val32), sharing one
+//   int32 column array.  sd = sqrt(diag), isd = 1/sd, dg = diag (double).
+//   fid[] maps each slot to its face (bit 31 set when the slot is the
+//   face's lower coefficient), so values can be refreshed without a repack.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ldupcg.h"
+
+namespace ldu {
+
+constexpr int kWarp = 32;
+constexpr int kNumDots = 4;            // doubles per block in a reduction slot
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr uint32_t kLowerBit = 0x80000000u;
+constexpr uint32_t kPadFid = 0xffffffffu;
+
+// error bits raised by device-side validation
+enum : int {
+    kFlagBadIndex = 1,
+    kFlagBadOrder = 2,
+    kFlagBadDiag = 4,
+    kFlagNonFinite = 8,
+};
+
+// device status words written by the persistent kernels
+enum : int {
+    kDevOk = 0,
+    kDevNotConverged = 1,
+    kDevNotSpd = 2,
+    kDevTimeout = 3,
+};
+
+struct SolveOut {
+    int status;
+    int iters;
+    int replacements;
+    int pad;
+    double relres;
+    double bnorm;
+};
+
+// Read-only view of the repacked matrix, passed by value to kernels.
+struct SellView {
+    int n;             // real rows
+    int n_pad;         // padded rows
+    int n_slices;
+    int C;             // rows per slice
+    const int *slice_ptr;   // [n_slices + 1], in slots
+    const int *slice_w;     // [n_slices]
+    const int *col;         // [nnz_pad]
+    const double *val64;    // [nnz_pad]
+    const float *val32;     // [nnz_pad]
+    const double *sd;       // [n_pad]
+    const double *isd;      // [n_pad]
+    const double *dg;       // [n_pad]
+};
+
+// Barrier state shared by the blocks of one persistent launch.
+struct GridSync {
+    unsigned *count;        // arrivals, reset to 0 before each launch
+    int *err;               // first error code raised
+    unsigned long long timeout_ns;
+};
+
+}  // namespace ldu
+
+// Host-side handle.  Plain struct: every pointer is a device allocation owned
+// by the handle unless noted.
+struct ldu_matrix {
+    int device;
+    int num_sms;
+    int64_t n, nf, n_pad, nnz_pad, n_slices;
+    int C;
+    int max_w;
+    int block_threads;
+    int blocks_per_sm;
+    int64_t device_bytes;
+    // structure
+    int *slice_ptr, *slice_w, *col;
+    uint32_t *fid;
+    int32_t *owner, *neighbour;
+    // values
+    double *val64, *sd, *isd, *dg;
+    float *val32;
+    // work vectors
+    double *v64[10];
+    float *v32[8];
+    double *slots;          // [2][max_grid][kNumDots]
+    int max_grid;
+    unsigned *bar_count;
+    int *bar_err;
+    ldu::SolveOut *out_dev;
+    ldu::SolveOut *out_host;   // pinned host
+    int *flags_dev;            // validation flags
+    ldu_solve_stats last;
+};
+
+namespace ldu {
+
+ldu::SellView view_of(const ldu_matrix *A);
+int cuda_status(cudaError_t e);
+int launch_persistent(const void *kernel, int grid, int block, void **args, cudaStream_t s);
+int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid);
+
+// ---------------------------------------------------------------------------
+// device helpers
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative launch.  `epoch` counts the barriers
+// this block has passed; arrivals accumulate in one counter that is never
+// reset during the launch.  Every spin is bounded: after timeout_ns the block
+// records kDevTimeout and all blocks leave at their next barrier.  Returns
+// false when the launch must stop.
+__device__ __forceinline__ bool grid_sync(const GridSync &g, unsigned &epoch) {
+    __shared__ int s_fail;
+    __syncthreads();
+    epoch += 1;
+    if (threadIdx.x == 0) {
+        const unsigned target = epoch * gridDim.x;
+        __threadfence();
+        atomicAdd(g.count, 1u);
+        int fail = 0;
+        const unsigned long long t0 = global_ns();
+        while ((int)(ld_acquire_u32(g.count) - target) < 0) {
+            if (*(volatile int *)g.err != 0) {
+                fail = 1;
+                break;
+            }
+            if (global_ns() - t0 > g.timeout_ns) {
+                atomicCAS(g.err, 0, kDevTimeout);
+                fail = 1;
+                break;
+            }
+            __nanosleep(40);
+        }
+        __threadfence();
+        if (*(volatile int *)g.err != 0)
+            fail = 1;
+        s_fail = fail;
+    }
+    __syncthreads();
+    return s_fail == 0;
+}
+
+template <int K>
+__device__ __forceinline__ void warp_sum(double (&v)[K]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            v[k] += __shfl_down_sync(kFullMask, v[k], o);
+}
+
+// Sum K doubles over the block (fixed order) and store them in slot[0..K).
+template <int K>
+__device__ __forceinline__ void block_sum_to_slot(double (&v)[K], double *slot) {
+    __shared__ double sm[32][K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    warp_sum<K>(v);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            sm[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+        double t[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            t[k] = lane < nwarps ? sm[lane][k] : 0.0;
+        warp_sum<K>(t);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                slot[k] = t[k];
+    }
+}
+
+// After a barrier: every block sums the per-block slots in the same fixed
+// order, so all blocks hold bitwise-identical totals.
+template <int K>
+__device__ __forceinline__ void grid_total(const double *slots, double (&out)[K]) {
+    __shared__ double res[K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        double t[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            t[k] = 0.0;
+        for (int c = lane; c < (int)gridDim.x; c += 32)
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                t[k] += __ldcg(slots + (size_t)c * kNumDots + k);
+        warp_sum<K>(t);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                res[k] = t[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        out[k] = res[k];
+}
+
+// ---- R-wide vector loads / stores of consecutive rows ----------------------
+
+template <typename T, int R>
+struct Rows {
+    T v[R];
+};
+
+template <int R>
+__device__ __forceinline__ void ld_rows(const float *p, float (&o)[R]) {
+    if constexpr (R == 4) {
+        float4 t = *reinterpret_cast<const float4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (R == 2) {
+        float2 t = *reinterpret_cast<const float2 *>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else {
+        o[0] = *p;
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void st_rows(float *p, const float (&o)[R]) {
+    if constexpr (R == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (R == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(o[0], o[1]);
+    } else {
+        *p = o[0];
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void ld_rows(const double *p, double (&o)[R]) {
+    if constexpr (R >= 2) {
+#pragma unroll
+        for (int j = 0; j < R; j += 2) {
+            double2 t = *reinterpret_cast<const double2 *>(p + j);
+            o[j] = t.x;
+            o[j + 1] = t.y;
+        }
+    } else {
+        o[0] = *p;
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void st_rows(double *p, const double (&o)[R]) {
+    if constexpr (R >= 2) {
+#pragma unroll
+        for (int j = 0; j < R; j += 2)
+            *reinterpret_cast<double2 *>(p + j) = make_double2(o[j], o[j + 1]);
+    } else {
+        *p = o[0];
+    }
+}
+
+// streaming (evict-first) loads for the matrix, which is read once per pass
+template <int R>
+__device__ __forceinline__ void ld_stream(const int *p, int (&o)[R]) {
+    if constexpr (R == 4) {
+        int4 t = __ldcs(reinterpret_cast<const int4 *>(p));
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (R == 2) {
+        int2 t = __ldcs(reinterpret_cast<const int2 *>(p));
+        o[0] = t.x; o[1] = t.y;
+    } else {
+        o[0] = __ldcs(p);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void ld_stream(const float *p, float (&o)[R]) {
+    if constexpr (R == 4) {
+        float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (R == 2) {
+        float2 t = __ldcs(reinterpret_cast<const float2 *>(p));
+        o[0] = t.x; o[1] = t.y;
+    } else {
+        o[0] = __ldcs(p);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void ld_stream(const double *p, double (&o)[R]) {
+    if constexpr (R >= 2) {
+#pragma unroll
+        for (int j = 0; j < R; j += 2) {
+            double2 t = __ldcs(reinterpret_cast<const double2 *>(p + j));
+            o[j] = t.x;
+            o[j + 1] = t.y;
+        }
+    } else {
+        o[0] = __ldcs(p);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ const T *vals_of(const SellView &A);
+template <>
+__device__ __forceinline__ const double *vals_of<double>(const SellView &A) { return A.val64; }
+template <>
+__device__ __forceinline__ const float *vals_of<float>(const SellView &A) { return A.val32; }
+
+// acc[j] += sum_k Ahat[row0 + j, col] * x[col] over the off-diagonal slots
+// of this lane's R rows in slice s.  Slots are taken KB at a time: all
+// column and value loads of a batch are issued before its gathers.
+template <typename T, int R, int KB>
+__device__ __forceinline__ void sell_accum(const SellView &A, int s, int lane,
+                                           const T *__restrict__ x, T (&acc)[R]) {
+    const int w = A.slice_w[s];
+    const int C = A.C;
+    const int base = A.slice_ptr[s] + R * lane;
+    const T *__restrict__ val = vals_of<T>(A);
+    for (int k0 = 0; k0 < w; k0 += KB) {
+        int c[KB][R];
+        T v[KB][R];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+            if (k0 + k < w) {
+                ld_stream<R>(A.col + base + (k0 + k) * C, c[k]);
+                ld_stream<R>(val + base + (k0 + k) * C, v[k]);
+            }
+        }
+        T g[KB][R];
+#pragma unroll
+        for (int k = 0; k < KB; ++k)
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                g[k][j] = (k0 + k < w) ? x[c[k][j]] : T(0);
+#pragma unroll
+        for (int k = 0; k < KB; ++k)
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (k0 + k < w)
+                    acc[j] = fma(v[k][j], g[k][j], acc[j]);
+    }
+}
+
+// Same, for two vectors gathered through the same slots (y1 = Ahat x1,
+// y2 = Ahat x2 share one read of the matrix).
+template <typename T, int R, int KB>
+__device__ __forceinline__ void sell_accum2(const SellView &A, int s, int lane,
+                                            const T *__restrict__ x1, const T *__restrict__ x2,
+                                            T (&acc1)[R], T (&acc2)[R]) {
+    const int w = A.slice_w[s];
+    const int C = A.C;
+    const int base = A.slice_ptr[s] + R * lane;
+    const T *__restrict__ val = vals_of<T>(A);
+    for (int k0 = 0; k0 < w; k0 += KB) {
+        int c[KB][R];
+        T v[KB][R];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+            if (k0 + k < w) {
+                ld_stream<R>(A.col + base + (k0 + k) * C, c[k]);
+                ld_stream<R>(val + base + (k0 + k) * C, v[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KB; ++k)
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (k0 + k < w) {
+                    acc1[j] = fma(v[k][j], x1[c[k][j]], acc1[j]);
+                    acc2[j] = fma(v[k][j], x2[c[k][j]], acc2[j]);
+                }
+    }
+}
+
+// Slices of the calling block: a contiguous range, warps interleaved in it.
+struct SliceRange {
+    int begin, end;
+};
+
+__device__ __forceinline__ SliceRange block_slices(int n_slices) {
+    const long long b = blockIdx.x, G = gridDim.x;
+    SliceRange r;
+    r.begin = (int)((b * n_slices) / G);
+    r.end = (int)(((b + 1) * n_slices) / G);
+    return r;
+}
+
+}  // namespace ldu

@@ -1,0 +1,257 @@
+"""Python binding of libldupcg: argument marshalling only.
+
+Every function here has the name of the C entry point it calls (see
+include/ldupcg.h) and does nothing but check tensor placement, pass device
+pointers and the current torch CUDA stream, and turn status codes into
+exceptions.  All arithmetic of the solve runs in the library's kernels; if
+the library is missing the import of this module succeeds but every call
+raises, so there is never a silent fallback.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+OK, NOT_CONVERGED = 0, 1
+ERR_BAD_ARG, ERR_BAD_ADDRESSING, ERR_NOT_SPD = -1, -2, -3
+ERR_CUDA, ERR_BARRIER_TIMEOUT, ERR_OOM, ERR_UNSUPPORTED = -4, -5, -6, -7
+FP64, FP32, MIXED = 0, 1, 2
+_PREC = {"fp64": FP64, "fp32": FP32, "mixed": MIXED, FP64: FP64, FP32: FP32, MIXED: MIXED}
+
+
+class LduError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+class LduOpts(ctypes.Structure):
+    _fields_ = [("slice_rows", ctypes.c_int), ("block_threads", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int)]
+
+
+class PcgOpts(ctypes.Structure):
+    _fields_ = [("rr_period", ctypes.c_int), ("tau", ctypes.c_double), ("restart", ctypes.c_int),
+                ("barrier_timeout_s", ctypes.c_double), ("fault_inject", ctypes.c_int)]
+
+
+class LduSolveStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("replacements", ctypes.c_int), ("relres", ctypes.c_double),
+                ("bnorm", ctypes.c_double), ("grid_blocks", ctypes.c_int),
+                ("block_threads", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LduInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("n_padded", ctypes.c_int64),
+                ("nnz_padded", ctypes.c_int64), ("slice_rows", ctypes.c_int),
+                ("n_slices", ctypes.c_int64), ("max_row_entries", ctypes.c_int),
+                ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libldupcg.so (built in-tree by build.py); raise if it is absent."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(path)
+        i, i64, d = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        pi, pd = ctypes.POINTER(i), ctypes.POINTER(d)
+        L.ldu_create.argtypes = [i64, i64, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(LduOpts), _vp,
+                                 ctypes.POINTER(_vp)]
+        L.ldu_update_values.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.ldu_set_face_coeffs.argtypes = [_vp, _vp, _vp, _vp]
+        L.ldu_spmv.argtypes = [_vp, i, _vp, _vp, _vp]
+        L.pcg_solve.argtypes = [_vp, _vp, _vp, d, i, pi, pd, _vp]
+        L.pipecg_solve.argtypes = [_vp, _vp, _vp, d, i, i, ctypes.POINTER(PcgOpts), pi, pd, _vp]
+        L.ldu_face_grad.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.ldu_last_stats.argtypes = [_vp, ctypes.POINTER(LduSolveStats)]
+        L.ldu_get_info.argtypes = [_vp, ctypes.POINTER(LduInfo)]
+        L.ldu_destroy.argtypes = [_vp]
+        L.ldu_destroy.restype = None
+        L.ldu_status_string.argtypes = [i]
+        L.ldu_status_string.restype = ctypes.c_char_p
+        for name in ("ldu_create", "ldu_update_values", "ldu_set_face_coeffs", "ldu_spmv",
+                     "pcg_solve", "pipecg_solve", "ldu_face_grad", "ldu_last_stats",
+                     "ldu_get_info"):
+            getattr(L, name).restype = i
+        _LIB = L
+    return _LIB
+
+
+def status_string(status):
+    try:
+        return lib().ldu_status_string(int(status)).decode()
+    except RuntimeError:
+        return "library not loaded"
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return _vp(s.cuda_stream)
+
+
+def _dev(t, dtype, n, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of {n} elements")
+    return _vp(t.data_ptr())
+
+
+def _check(status, what, allow_not_converged=True):
+    if status == OK or (status == NOT_CONVERGED and allow_not_converged):
+        return status
+    raise LduError(status, what)
+
+
+class LduMatrix:
+    """A device-resident handle of one LDU matrix (owner of its allocations)."""
+
+    def __init__(self, handle, n, nfaces, device):
+        self._h = handle
+        self.n = n
+        self.nfaces = nfaces
+        self.device = device
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("LduMatrix was destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ldu_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        out = LduInfo()
+        _check(lib().ldu_get_info(self.handle, ctypes.byref(out)), "ldu_get_info")
+        return out.as_dict()
+
+    def stats(self):
+        out = LduSolveStats()
+        _check(lib().ldu_last_stats(self.handle, ctypes.byref(out)), "ldu_last_stats")
+        return out.as_dict()
+
+
+def ldu_create(n, owner, neighbour, diag, upper, lower, slice_rows=0, block_threads=0,
+               blocks_per_sm=0, stream=None):
+    """Create a handle from device tensors (int32 owner/neighbour, float64 values)."""
+    nf = owner.numel()
+    args = [ctypes.c_int64(n), ctypes.c_int64(nf),
+            _dev(owner, torch.int32, nf, "owner"), _dev(neighbour, torch.int32, nf, "neighbour"),
+            _dev(diag, torch.float64, n, "diag"), _dev(upper, torch.float64, nf, "upper"),
+            _dev(lower, torch.float64, nf, "lower")]
+    opts = LduOpts(slice_rows, block_threads, blocks_per_sm)
+    h = _vp()
+    st = lib().ldu_create(*args, ctypes.byref(opts), _stream(stream), ctypes.byref(h))
+    _check(st, "ldu_create", allow_not_converged=False)
+    return LduMatrix(h, n, nf, diag.device)
+
+
+def ldu_update_values(A, diag, upper, lower, stream=None):
+    st = lib().ldu_update_values(A.handle, _dev(diag, torch.float64, A.n, "diag"),
+                                 _dev(upper, torch.float64, A.nfaces, "upper"),
+                                 _dev(lower, torch.float64, A.nfaces, "lower"), _stream(stream))
+    _check(st, "ldu_update_values", allow_not_converged=False)
+
+
+def ldu_set_face_coeffs(A, coef, diag_extra, stream=None):
+    st = lib().ldu_set_face_coeffs(A.handle, _dev(coef, torch.float64, A.nfaces, "coef"),
+                                   _dev(diag_extra, torch.float64, A.n, "diag_extra"),
+                                   _stream(stream))
+    _check(st, "ldu_set_face_coeffs", allow_not_converged=False)
+
+
+def ldu_spmv(A, x, y=None, precision="fp64", stream=None):
+    p = _PREC[precision]
+    dt = torch.float64 if p == FP64 else torch.float32
+    if y is None:
+        y = torch.empty(A.n, dtype=dt, device=x.device)
+    st = lib().ldu_spmv(A.handle, p, _dev(x, dt, A.n, "x"), _dev(y, dt, A.n, "y"), _stream(stream))
+    _check(st, "ldu_spmv", allow_not_converged=False)
+    return y
+
+
+def pcg_solve(A, b, x=None, tol=1e-8, maxit=20000, stream=None, check=True):
+    """Jacobi-PCG; x (in: initial guess, out: solution) is allocated if None.
+    Returns (x, status, iters, relres)."""
+    if x is None:
+        x = torch.zeros(A.n, dtype=torch.float64, device=b.device)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().pcg_solve(A.handle, _dev(b, torch.float64, A.n, "b"),
+                         _dev(x, torch.float64, A.n, "x"), float(tol), int(maxit),
+                         ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+    if check:
+        _check(st, "pcg_solve")
+    return x, st, it.value, rr.value
+
+
+def pipecg_solve(A, b, x=None, tol=1e-8, maxit=20000, precision="fp64", rr_period=0, tau=0.0,
+                 restart=False, barrier_timeout_s=0.0, fault_inject=0, stream=None, check=True):
+    """Pipelined Jacobi-PCG (precision 'fp64' or 'mixed').
+    Returns (x, status, iters, relres)."""
+    if x is None:
+        x = torch.zeros(A.n, dtype=torch.float64, device=b.device)
+    opts = PcgOpts(int(rr_period), float(tau), int(bool(restart)), float(barrier_timeout_s),
+                   int(fault_inject))
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().pipecg_solve(A.handle, _dev(b, torch.float64, A.n, "b"),
+                            _dev(x, torch.float64, A.n, "x"), float(tol), int(maxit),
+                            _PREC[precision], ctypes.byref(opts), ctypes.byref(it),
+                            ctypes.byref(rr), _stream(stream))
+    if check:
+        _check(st, "pipecg_solve")
+    return x, st, it.value, rr.value
+
+
+def ldu_face_grad(A, lam, x, out=None, stream=None):
+    if out is None:
+        out = torch.empty(A.nfaces, dtype=torch.float64, device=x.device)
+    st = lib().ldu_face_grad(A.handle, _dev(lam, torch.float64, A.n, "lambda"),
+                             _dev(x, torch.float64, A.n, "x"),
+                             _dev(out, torch.float64, A.nfaces, "dcoef"), _stream(stream))
+    _check(st, "ldu_face_grad", allow_not_converged=False)
+    return out
+
+
+def ldu_destroy(A):
+    A.close()
+
+
+def from_system(sys_, device="cuda", **opts):
+    """Upload an ldu_cases.LduSystem and create its handle (inputs only)."""
+    t = lambda a, dt: torch.as_tensor(a).to(device=device, dtype=dt).contiguous()  # noqa: E731
+    A = ldu_create(sys_.n, t(sys_.owner, torch.int32), t(sys_.neighbour, torch.int32),
+                   t(sys_.diag, torch.float64), t(sys_.upper, torch.float64),
+                   t(sys_.lower, torch.float64), **opts)
+    return A

@@ -1,0 +1,293 @@
+"""GPU parity of the C-ABI path against the oracle: SpMV, Jacobi-PCG,
+pipelined PCG (FP64 and mixed), face gradient, value refresh, edge cases.
+
+Tolerances (floating point, from the arithmetic):
+  * SpMV FP64: |y - y_ref| <= 1e-13 * (|A| |x|)_i per row (componentwise
+    backward-error form; a few ulps of the row's absolute sum).
+  * SpMV FP32: <= 1e-6 * (|A| |x|)_i on float inputs.
+  * Solves: the true ||b - A x||/||b|| of the returned x, recomputed by the
+    oracle's own FP64 SpMV, is <= tol (1% slack for the difference between
+    the scaled-space and original-space rounding); iteration counts of the
+    FP64 methods within 2% + 2 of the oracle's; solutions at a tight
+    tolerance within 1e-9 of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import ldu_cases as lc
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_1505_07630_gb300 as p
+    return p
+
+
+def cuda(a, dt=None):
+    t = torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    return t if dt is None else t.to(dt)
+
+
+def abs_bound(oracle_mod, s, x):
+    return oracle_mod.spmv(s, np.abs(x), diag=np.abs(s.diag), upper=np.abs(s.upper),
+                           lower=np.abs(s.lower))
+
+
+def shuffled_faces(s, seed=5):
+    g = np.random.default_rng(seed)
+    order = g.permutation(s.nfaces)
+    t = lc.LduSystem(n=s.n, owner=s.owner[order], neighbour=s.neighbour[order], diag=s.diag,
+                     upper=s.upper[order], lower=s.lower[order], b=s.b, coef=s.coef[order],
+                     diag_extra=s.diag_extra, shape=s.shape, name=s.name + "-shuffled")
+    return t
+
+
+def nonsymmetric(s, seed=9):
+    g = np.random.default_rng(seed)
+    t = lc.LduSystem(n=s.n, owner=s.owner, neighbour=s.neighbour,
+                     diag=s.diag * g.uniform(1.0, 2.0, s.n),
+                     upper=s.upper * g.uniform(0.5, 1.5, s.nfaces),
+                     lower=s.lower * g.uniform(0.5, 1.5, s.nfaces), b=s.b, coef=s.coef,
+                     diag_extra=s.diag_extra, shape=s.shape, name=s.name + "-nonsym")
+    return t
+
+
+SPMV_CASES = {
+    "c1-8": lambda: lc.config1(s=8),
+    "c2-13-ragged": lambda: lc.config2(s=13),
+    "c3-10": lambda: lc.config3(s=10),
+    "box-5x6x7": lambda: lc.poisson_box(5, 6, 7, diffusivity="lognormal"),
+    "one-cell": lambda: lc.poisson_box(1, 1, 1),
+    "line-1x1x9": lambda: lc.poisson_box(9, 1, 1),
+    "shuffled": lambda: shuffled_faces(lc.config2(s=7)),
+    "nonsym": lambda: nonsymmetric(lc.config2(s=9)),
+}
+
+
+@pytest.mark.parametrize("case", list(SPMV_CASES))
+@pytest.mark.parametrize("C", [32, 64, 128])
+def test_spmv_parity(pkg, oracle_mod, case, C):
+    s = SPMV_CASES[case]()
+    A = pkg.from_system(s, slice_rows=C)
+    g = np.random.default_rng(3)
+    x = g.uniform(-1, 1, s.n)
+    y = pkg.ldu_spmv(A, cuda(x)).cpu().numpy()
+    y_ref = oracle_mod.spmv(s, x)
+    bound = abs_bound(oracle_mod, s, x)
+    assert np.all(np.abs(y - y_ref) <= 1e-13 * bound + 1e-300)
+    x32 = x.astype(np.float32)
+    y32 = pkg.ldu_spmv(A, cuda(x32), precision="fp32").cpu().numpy().astype(np.float64)
+    y32_ref = oracle_mod.spmv(s, x32.astype(np.float64))
+    bound32 = abs_bound(oracle_mod, s, x32.astype(np.float64))
+    assert np.all(np.abs(y32 - y32_ref) <= 1e-6 * bound32 + 1e-30)
+    info = A.info()
+    assert info["n"] == s.n and info["n_padded"] % C == 0 and info["n_padded"] >= s.n
+    A.close()
+
+
+SOLVE_CASES = {
+    "c1-16": lambda: lc.config1(s=16),
+    "c2-20": lambda: lc.config2(s=20),
+    "c3-16": lambda: lc.config3(s=16),
+    "box-7x5x9": lambda: lc.poisson_box(7, 5, 9, diffusivity="lognormal", seed=4),
+    "shuffled-c2-9": lambda: shuffled_faces(lc.config2(s=9)),
+}
+
+
+@pytest.mark.parametrize("case", list(SOLVE_CASES))
+@pytest.mark.parametrize("C", [32, 128])
+def test_pcg_parity(pkg, oracle_mod, case, C):
+    s = SOLVE_CASES[case]()
+    A = pkg.from_system(s, slice_rows=C)
+    b = cuda(s.b)
+    ref = oracle_mod.pcg(s, tol=1e-8)
+    x, st, it, rr = pkg.pcg_solve(A, b, tol=1e-8)
+    xh = x.cpu().numpy()
+    true_rr = oracle_mod.true_relres(s, xh)
+    assert st == 0
+    assert true_rr <= 1.01e-8
+    assert abs(rr - true_rr) <= 1e-3 * true_rr + 1e-15
+    assert abs(it - ref.iters) <= 0.02 * ref.iters + 2
+    # tight solve: the same solution as the oracle's
+    xt, st, _, _ = pkg.pcg_solve(A, b, tol=1e-12)
+    xs = oracle_mod.pcg(s, tol=1e-12).x
+    assert st == 0
+    assert np.linalg.norm(xt.cpu().numpy() - xs) <= 1e-9 * np.linalg.norm(xs)
+    A.close()
+
+
+@pytest.mark.parametrize("case", list(SOLVE_CASES))
+def test_pipecg_fp64_parity(pkg, oracle_mod, case):
+    s = SOLVE_CASES[case]()
+    A = pkg.from_system(s)
+    b = cuda(s.b)
+    ref = oracle_mod.pipecg(s, tol=1e-8)
+    x, st, it, rr = pkg.pipecg_solve(A, b, tol=1e-8, precision="fp64")
+    true_rr = oracle_mod.true_relres(s, x.cpu().numpy())
+    assert st == 0 and true_rr <= 1.01e-8
+    assert abs(it - ref.iters) <= 0.02 * ref.iters + 2
+    pcg_it = oracle_mod.pcg(s, tol=1e-8).iters
+    assert abs(it - pcg_it) <= 0.02 * pcg_it + 2      # pipelined == PCG in exact arithmetic
+    A.close()
+
+
+@pytest.mark.parametrize("case", list(SOLVE_CASES))
+@pytest.mark.parametrize("mode", [dict(rr_period=16), dict(rr_period=0, tau=1e-3, restart=True)])
+def test_mixed_parity(pkg, oracle_mod, case, mode):
+    s = SOLVE_CASES[case]()
+    A = pkg.from_system(s)
+    b = cuda(s.b)
+    ref = oracle_mod.mixed_pipecg(s, tol=1e-8, period=mode["rr_period"],
+                                  tau=mode.get("tau", 0.0), restart=mode.get("restart", False))
+    x, st, it, rr = pkg.pipecg_solve(A, b, tol=1e-8, precision="mixed", **mode)
+    xh = x.cpu().numpy()
+    true_rr = oracle_mod.true_relres(s, xh)
+    assert st == 0 and true_rr <= 1.01e-8, (st, it, rr, true_rr)
+    # float rounding differs in order between the two, so iteration counts
+    # agree loosely; the error against the tight FP64 solution is reported
+    assert it <= 1.25 * ref.iters + 8
+    xs = oracle_mod.pcg(s, tol=1e-13).x
+    err = np.linalg.norm(xh - xs) / np.linalg.norm(xs)
+    err_ref = np.linalg.norm(ref.x - xs) / np.linalg.norm(xs)
+    assert err <= max(10 * err_ref, 1e-6)
+    A.close()
+
+
+def test_mixed_reaches_tight_tolerance(pkg, oracle_mod):
+    s = lc.config2(s=12)
+    A = pkg.from_system(s)
+    x, st, it, rr = pkg.pipecg_solve(A, cuda(s.b), tol=1e-12, precision="mixed")
+    assert st == 0 and oracle_mod.true_relres(s, x.cpu().numpy()) <= 1.01e-12
+    assert A.stats()["replacements"] >= 3
+    A.close()
+
+
+@pytest.mark.parametrize("solver", ["pcg", "pipe", "mixed"])
+def test_edge_cases(pkg, oracle_mod, solver):
+    s = lc.config2(s=6)
+    A = pkg.from_system(s)
+
+    def solve(b, x0=None, **kw):
+        if solver == "pcg":
+            return pkg.pcg_solve(A, b, x0, check=False, **kw)
+        return pkg.pipecg_solve(A, b, x0, precision="fp64" if solver == "pipe" else "mixed",
+                                check=False, **kw)
+
+    # zero right-hand side: x = 0 whatever the initial guess
+    x, st, it, rr = solve(torch.zeros(s.n, dtype=torch.float64, device="cuda"),
+                          torch.ones(s.n, dtype=torch.float64, device="cuda"))
+    assert st == 0 and rr == 0.0 and it == 0 and float(x.abs().max()) == 0.0
+    # exact initial guess: no iterations
+    xs = oracle_mod.pcg(s, tol=1e-14).x
+    x, st, it, rr = solve(cuda(s.b), cuda(xs), tol=1e-8)
+    assert st == 0 and it == 0 and rr <= 1e-8
+    # iteration cap
+    x, st, it, rr = solve(cuda(s.b), tol=1e-14, maxit=3)
+    assert st == 1 and it == 3 and rr > 1e-14
+    assert abs(oracle_mod.true_relres(s, x.cpu().numpy()) - rr) <= 1e-6 * rr
+    # deterministic: two runs agree bitwise
+    x1, *_ = solve(cuda(s.b), tol=1e-10)
+    x2, *_ = solve(cuda(s.b), tol=1e-10)
+    assert torch.equal(x1, x2)
+    A.close()
+
+
+def test_empty_and_tiny(pkg, oracle_mod):
+    s = lc.poisson_box(1, 1, 1)
+    A = pkg.from_system(s)
+    x, st, it, rr = pkg.pcg_solve(A, cuda(s.b), tol=1e-12)
+    assert st == 0 and abs(float(x[0]) - s.b[0] / s.diag[0]) <= 1e-15 * abs(s.b[0] / s.diag[0])
+    A.close()
+    e = torch.zeros(0, dtype=torch.float64, device="cuda")
+    ei = torch.zeros(0, dtype=torch.int32, device="cuda")
+    A0 = pkg.ldu_create(0, ei, ei, e, e, e)
+    x, st, it, rr = pkg.pcg_solve(A0, e)
+    assert st == 0 and it == 0
+    A0.close()
+
+
+def test_not_spd_and_bad_addressing(pkg):
+    s = lc.poisson_box(6, 5, 4)
+    ones = np.ones(s.n)
+    # unit diagonal, off-diagonals -1: I - adjacency is indefinite
+    t = lc.LduSystem(n=s.n, owner=s.owner, neighbour=s.neighbour, diag=ones,
+                     upper=-np.ones(s.nfaces), lower=-np.ones(s.nfaces), b=s.b, coef=s.coef,
+                     diag_extra=s.diag_extra)
+    A = pkg.from_system(t)
+    for call in (lambda: pkg.pcg_solve(A, cuda(s.b), check=False),
+                 lambda: pkg.pipecg_solve(A, cuda(s.b), check=False)):
+        _, st, _, _ = call()
+        assert st == pkg.ldupcg.ERR_NOT_SPD
+    A.close()
+    with pytest.raises(pkg.LduError) as e:
+        bad = lc.LduSystem(n=s.n, owner=s.neighbour, neighbour=s.owner, diag=s.diag,
+                           upper=s.upper, lower=s.lower, b=s.b, coef=s.coef,
+                           diag_extra=s.diag_extra)
+        pkg.from_system(bad)
+    assert e.value.status == pkg.ldupcg.ERR_BAD_ADDRESSING
+    with pytest.raises(pkg.LduError) as e:
+        nb = s.neighbour.copy()
+        nb[3] = s.n + 7
+        bad = lc.LduSystem(n=s.n, owner=s.owner, neighbour=nb, diag=s.diag, upper=s.upper,
+                           lower=s.lower, b=s.b, coef=s.coef, diag_extra=s.diag_extra)
+        pkg.from_system(bad)
+    assert e.value.status == pkg.ldupcg.ERR_BAD_ADDRESSING
+    with pytest.raises(pkg.LduError) as e:
+        d = s.diag.copy()
+        d[0] = 0.0
+        bad = lc.LduSystem(n=s.n, owner=s.owner, neighbour=s.neighbour, diag=d, upper=s.upper,
+                           lower=s.lower, b=s.b, coef=s.coef, diag_extra=s.diag_extra)
+        pkg.from_system(bad)
+    assert e.value.status == pkg.ldupcg.ERR_NOT_SPD
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_barrier_timeout_is_reported_and_recoverable(pkg, oracle_mod, precision):
+    s = lc.config1(s=10)
+    A = pkg.from_system(s)
+    _, st, _, _ = pkg.pipecg_solve(A, cuda(s.b), precision=precision, barrier_timeout_s=0.2,
+                                   fault_inject=1, check=False)
+    assert st == pkg.ldupcg.ERR_BARRIER_TIMEOUT
+    # the context and the handle stay usable
+    x, st, it, rr = pkg.pipecg_solve(A, cuda(s.b), precision=precision, tol=1e-8)
+    assert st == 0 and oracle_mod.true_relres(s, x.cpu().numpy()) <= 1.01e-8
+    A.close()
+
+
+def test_face_grad_bitwise(pkg, oracle_mod):
+    s = lc.config2(s=11)
+    A = pkg.from_system(s)
+    g = np.random.default_rng(2)
+    lam = g.standard_normal(s.n)
+    x = g.standard_normal(s.n)
+    got = pkg.ldu_face_grad(A, cuda(lam), cuda(x)).cpu().numpy()
+    ref = oracle_mod.face_grad(s.owner, s.neighbour, lam, x)
+    assert np.array_equal(got, ref)
+    A.close()
+
+
+def test_set_face_coeffs_matches_assembly(pkg, oracle_mod):
+    s = lc.config2(s=10)
+    A = pkg.from_system(s)
+    g = np.random.default_rng(4)
+    coef = s.coef * g.uniform(0.5, 2.0, s.nfaces)
+    pkg.ldu_set_face_coeffs(A, cuda(coef), cuda(s.diag_extra))
+    d, u, lo = oracle_mod.matrix_from_coef(s, coef)
+    x = g.uniform(-1, 1, s.n)
+    y = pkg.ldu_spmv(A, cuda(x)).cpu().numpy()
+    y_ref = oracle_mod.spmv(s, x, diag=d, upper=u, lower=lo)
+    bound = oracle_mod.spmv(s, np.abs(x), diag=np.abs(d), upper=np.abs(u), lower=np.abs(lo))
+    assert np.all(np.abs(y - y_ref) <= 1e-13 * bound)
+    # update_values with the same matrix gives the same product
+    pkg.ldu_update_values(A, cuda(d), cuda(u), cuda(lo))
+    y2 = pkg.ldu_spmv(A, cuda(x)).cpu().numpy()
+    assert np.all(np.abs(y2 - y_ref) <= 1e-13 * bound)
+    A.close()
