@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
 
     double b2[1] = {0.0}, t1[1];
     prep_pass<R>(P, bh, xh, b2);
+    zero_rows<double, R>(P, p);   // the first p = r + 0 * p must not see stale values
     if (!reduce_grid<1>(P, b2, t1, epoch, parity))
         return;
     const double bnorm = sqrt(t1[0]);
