@@ -65,219 +65,9 @@ int launch_persistent(const void *kernel, int grid, int block, void **args, cuda
 
 }  // namespace ldu
 
+#include "setup_kernels.cuh"
+
 namespace {
-
-__global__ void k_validate_count(int64_t nf, int n, const int32_t *__restrict__ own,
-                                 const int32_t *__restrict__ nbr, int *deg, int *flags) {
-    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
-         f += (int64_t)gridDim.x * blockDim.x) {
-        const int o = own[f], nb = nbr[f];
-        if (o < 0 || nb < 0 || o >= n || nb >= n) {
-            atomicOr(flags, kFlagBadIndex);
-            continue;
-        }
-        if (o >= nb) {
-            atomicOr(flags, kFlagBadOrder);
-            continue;
-        }
-        atomicAdd(deg + o, 1);
-        atomicAdd(deg + nb, 1);
-    }
-}
-
-__global__ void k_validate_values(int64_t n, int64_t nf, const double *diag, const double *up,
-                                  const double *lo, int *flags) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const double d = diag[i];
-        if (!isfinite(d))
-            atomicOr(flags, kFlagNonFinite);
-        else if (!(d > 0.0))
-            atomicOr(flags, kFlagBadDiag);
-    }
-    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += stride)
-        if (!isfinite(up[f]) || !isfinite(lo[f]))
-            atomicOr(flags, kFlagNonFinite);
-}
-
-// one thread per slice: width = max degree of its rows
-__global__ void k_slice_width(int n, int n_slices, int C, const int *deg, int *slice_w) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_slices)
-        return;
-    int w = 0;
-    for (int i = 0; i < C; ++i) {
-        const int r = s * C + i;
-        if (r < n)
-            w = max(w, deg[r]);
-    }
-    slice_w[s] = w;
-}
-
-// padding everywhere first: col = own row, fid = pad
-__global__ void k_fill_pad(int n_pad, int C, const int *slice_ptr, const int *slice_w, int *col,
-                           uint32_t *fid) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_pad)
-        return;
-    const int s = r / C, i = r - s * C;
-    const int w = slice_w[s];
-    for (int k = 0; k < w; ++k) {
-        const int at = slice_ptr[s] + k * C + i;
-        col[at] = r;
-        fid[at] = kPadFid;
-    }
-}
-
-__global__ void k_scatter_faces(int64_t nf, int C, const int32_t *__restrict__ own,
-                                const int32_t *__restrict__ nbr, const int *slice_ptr, int *cursor,
-                                int *col, uint32_t *fid) {
-    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
-         f += (int64_t)gridDim.x * blockDim.x) {
-        const int o = own[f], nb = nbr[f];
-        int k = atomicAdd(cursor + o, 1);
-        int at = slice_ptr[o / C] + k * C + (o % C);
-        col[at] = nb;
-        fid[at] = (uint32_t)f;
-        k = atomicAdd(cursor + nb, 1);
-        at = slice_ptr[nb / C] + k * C + (nb % C);
-        col[at] = o;
-        fid[at] = (uint32_t)f | kLowerBit;
-    }
-}
-
-// insertion sort of each row's real slots by (column, face id)
-__global__ void k_sort_rows(int n, int C, const int *slice_ptr, const int *deg, int *col,
-                            uint32_t *fid) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n)
-        return;
-    const int s = r / C, i = r - s * C;
-    const int base = slice_ptr[s] + i;
-    const int d = deg[r];
-    for (int a = 1; a < d; ++a) {
-        const int ca = col[base + a * C];
-        const uint32_t fa = fid[base + a * C];
-        int b = a - 1;
-        while (b >= 0) {
-            const int cb = col[base + b * C];
-            const uint32_t fb = fid[base + b * C];
-            if (cb < ca || (cb == ca && (fb & ~kLowerBit) <= (fa & ~kLowerBit)))
-                break;
-            col[base + (b + 1) * C] = cb;
-            fid[base + (b + 1) * C] = fb;
-            --b;
-        }
-        col[base + (b + 1) * C] = ca;
-        fid[base + (b + 1) * C] = fa;
-    }
-}
-
-// diagonal scaling factors; padded rows get sd = isd = 1, dg = 0
-__global__ void k_diag_scale(int n, int n_pad, const double *diag, double *sd, double *isd,
-                             double *dg, int *flags) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_pad)
-        return;
-    if (r < n) {
-        const double d = diag[r];
-        if (!(d > 0.0) || !isfinite(d))
-            atomicOr(flags, kFlagBadDiag);
-        const double q = sqrt(d);
-        sd[r] = q;
-        isd[r] = 1.0 / q;
-        dg[r] = d;
-    } else {
-        sd[r] = 1.0;
-        isd[r] = 1.0;
-        dg[r] = 0.0;
-    }
-}
-
-// diag[r] = extra[r] + sum of coef over the row's faces, in slot order
-__global__ void k_diag_from_coef(int n, int n_pad, int C, const int *slice_ptr, const int *slice_w,
-                                 const uint32_t *fid, const double *coef, const double *extra,
-                                 double *sd, double *isd, double *dg, int *flags) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_pad)
-        return;
-    if (r >= n) {
-        sd[r] = 1.0;
-        isd[r] = 1.0;
-        dg[r] = 0.0;
-        return;
-    }
-    const int s = r / C, i = r - s * C;
-    const int w = slice_w[s];
-    double d = extra[r];
-    for (int k = 0; k < w; ++k) {
-        const uint32_t f = fid[slice_ptr[s] + k * C + i];
-        if (f != kPadFid)
-            d += coef[f & ~kLowerBit];
-    }
-    if (!(d > 0.0) || !isfinite(d))
-        atomicOr(flags, kFlagBadDiag);
-    const double q = sqrt(d);
-    sd[r] = q;
-    isd[r] = 1.0 / q;
-    dg[r] = d;
-}
-
-// scaled off-diagonal values of every slot.  coef != nullptr: a = -coef[f];
-// else a = upper[f] (owner row) or lower[f] (neighbour row).
-__global__ void k_values(int n_pad, int C, const int *slice_ptr, const int *slice_w, const int *col,
-                         const uint32_t *fid, const double *up, const double *lo,
-                         const double *coef, const double *sd, double *v64, float *v32) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_pad)
-        return;
-    const int s = r / C, i = r - s * C;
-    const int w = slice_w[s];
-    const double sr = sd[r];
-    for (int k = 0; k < w; ++k) {
-        const int at = slice_ptr[s] + k * C + i;
-        const uint32_t f = fid[at];
-        double v = 0.0;
-        if (f != kPadFid) {
-            const uint32_t face = f & ~kLowerBit;
-            const double a = coef ? -coef[face] : ((f & kLowerBit) ? lo[face] : up[face]);
-            v = a / (sr * sd[col[at]]);
-        }
-        v64[at] = v;
-        v32[at] = (float)v;
-    }
-}
-
-// y = A x = D^1/2 (I + Ahat_off) D^1/2 x, one thread per row (caller buffers
-// hold exactly n entries)
-template <typename T>
-__global__ void k_spmv(int n, int C, const int *slice_ptr, const int *slice_w, const int *col,
-                       const T *val, const double *sd, const T *__restrict__ x, T *__restrict__ y) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n)
-        return;
-    const int s = r / C, i = r - s * C;
-    const int w = slice_w[s];
-    const T sr = (T)sd[r];
-    T acc = sr * x[r];
-    for (int k = 0; k < w; ++k) {
-        const int at = slice_ptr[s] + k * C + i;
-        const int c = col[at];
-        if (c < n)
-            acc = fma(val[at], (T)sd[c] * x[c], acc);
-    }
-    y[r] = sr * acc;
-}
-
-__global__ void k_face_grad(int64_t nf, const int32_t *__restrict__ own,
-                            const int32_t *__restrict__ nbr, const double *__restrict__ lam,
-                            const double *__restrict__ x, double *__restrict__ g) {
-    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
-         f += (int64_t)gridDim.x * blockDim.x) {
-        const int o = own[f], nb = nbr[f];
-        g[f] = -(lam[o] - lam[nb]) * (x[o] - x[nb]);
-    }
-}
 
 int blocks_for(int64_t work, int threads) {
     int64_t b = (work + threads - 1) / threads;
