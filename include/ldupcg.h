@@ -202,6 +202,31 @@ void ldu_destroy(ldu_matrix *A);
 /* A static string naming a status code. */
 const char *ldu_status_string(int status);
 
+/* Jacobi-PCG on a small LDU system without any device allocation.  The paper
+ * has no counterpart: this exists for callers that cannot call cudaMalloc
+ * (their device memory is owned by another allocator, such as a framework's
+ * caching pool or a fixed-budget runtime, or they cannot afford cudaMalloc's
+ * implicit device synchronisation) and therefore cannot create a handle.
+ * It repacks the caller's arrays and runs the same kernel as pcg_solve with
+ * the same layout and launch shape, so the result equals pcg_solve's on a
+ * default handle.  All intermediate data live in one fixed-size __device__
+ * array (about 8.9 MB) that every GPU loading the library holds until the
+ * process exits; on each device the first call looks up its address
+ * (cudaGetSymbolAddress) with that device current.
+ *   n <= 32768 cells, nFaces <= 131072, at most 262144 stored off-diagonal
+ *   slots (8 per row on average, padding included); larger inputs return
+ *   LDU_ERR_UNSUPPORTED without doing any work.
+ *   owner, neighbour, diag, upper, lower, b: device arrays as in ldu_create
+ *   and pcg_solve; x: device double[n], initial guess in, solution out;
+ *   iters, relres: host, may be NULL.
+ * Every call on a device shares the scratch array and clears what it needs
+ * zeroed; calls whose work overlaps on the GPU (other streams or threads)
+ * race on it.  Synchronises stream.  Errors as ldu_create and pcg_solve. */
+int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *owner,
+                          const int32_t *neighbour, const double *diag, const double *upper,
+                          const double *lower, const double *b, double *x, double tol, int maxit,
+                          int *iters, double *relres, ldu_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

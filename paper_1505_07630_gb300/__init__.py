@@ -6,4 +6,5 @@ and the autograd wrapper.  PyTorch supplies device memory and streams only.
 """
 from .ldupcg import (LduError, LduMatrix, from_system, ldu_create, ldu_destroy,  # noqa: F401
                      ldu_face_grad, ldu_set_face_coeffs, ldu_spmv, ldu_update_values, lib,
-                     library_path, pcg_solve, pipecg_solve, status_string)
+                     library_path, pcg_solve, pcg_solve_ldu_noalloc, pipecg_solve,
+                     status_string)

@@ -33,6 +33,7 @@ enum : int {
     kFlagBadOrder = 2,
     kFlagBadDiag = 4,
     kFlagNonFinite = 8,
+    kFlagOverflow = 16,
 };
 
 // device status words written by the persistent kernels

@@ -88,6 +88,9 @@ def lib():
         L.ldu_get_info.argtypes = [_vp, ctypes.POINTER(LduInfo)]
         L.ldu_destroy.argtypes = [_vp]
         L.ldu_destroy.restype = None
+        L.pcg_solve_ldu_noalloc.argtypes = [i64, i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, d, i,
+                                            pi, pd, _vp]
+        L.pcg_solve_ldu_noalloc.restype = i
         L.ldu_status_string.argtypes = [i]
         L.ldu_status_string.restype = ctypes.c_char_p
         for name in ("ldu_create", "ldu_update_values", "ldu_set_face_coeffs", "ldu_spmv",
@@ -242,6 +245,25 @@ def ldu_face_grad(A, lam, x, out=None, stream=None):
                              _dev(out, torch.float64, A.nfaces, "dcoef"), _stream(stream))
     _check(st, "ldu_face_grad", allow_not_converged=False)
     return out
+
+
+def pcg_solve_ldu_noalloc(n, owner, neighbour, diag, upper, lower, b, x, tol=1e-8, maxit=20000,
+                          stream=None, check=True):
+    """Jacobi-PCG straight from device LDU arrays, using only the library's
+    fixed device scratch (no allocation; n <= 32768).  Returns
+    (x, status, iters, relres)."""
+    nf = owner.numel()
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().pcg_solve_ldu_noalloc(
+        ctypes.c_int64(n), ctypes.c_int64(nf), _dev(owner, torch.int32, nf, "owner"),
+        _dev(neighbour, torch.int32, nf, "neighbour"), _dev(diag, torch.float64, n, "diag"),
+        _dev(upper, torch.float64, nf, "upper"), _dev(lower, torch.float64, nf, "lower"),
+        _dev(b, torch.float64, n, "b"), _dev(x, torch.float64, n, "x"), float(tol), int(maxit),
+        ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+    if check:
+        _check(st, "pcg_solve_ldu_noalloc")
+    return x, st, it.value, rr.value
 
 
 def ldu_destroy(A):
