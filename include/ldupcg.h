@@ -87,6 +87,10 @@ typedef struct pcg_opts {
                                returns before its first barrier, so the others
                                time out and the call returns
                                LDU_ERR_BARRIER_TIMEOUT; 0 otherwise */
+    int deflate;            /* LDU_MIXED: 1 = deflate the constant vector (deflated
+                               CG, Saad et al. 2000): removes the near-null mode of
+                               pure-Neumann systems with a reference cell, which
+                               float recurrences cannot resolve; 0 = off (default) */
 } pcg_opts;
 
 /* Counters of the last solve on a handle. */
@@ -210,7 +214,7 @@ const char *ldu_status_string(int status);
  * It repacks the caller's arrays and runs the same kernel as pcg_solve with
  * the same layout and launch shape, so the result equals pcg_solve's on a
  * default handle.  All intermediate data live in one fixed-size __device__
- * array (about 8.9 MB) that every GPU loading the library holds until the
+ * array (8,130,816 bytes (7.75 MiB)) that every GPU loading the library holds until the
  * process exits; on each device the first call looks up its address
  * (cudaGetSymbolAddress) with that device current.
  *   n <= 32768 cells, nFaces <= 131072, at most 262144 stored off-diagonal

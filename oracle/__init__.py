@@ -39,7 +39,7 @@ def lib():
         L.or_pipecg.argtypes = mat + [_d, _d, c_double, c_int, c_int, pint, _d, _d]
         L.or_pipecg.restype = c_int
         L.or_mixed_pipecg.argtypes = mat + [_d, _d, c_double, c_int, c_double, c_int, c_int,
-                                            pint, pint, _d]
+                                            c_int, pint, pint, _d]
         L.or_mixed_pipecg.restype = c_int
         L.or_face_grad.argtypes = [i64, _i32, _i32, _d, _d, _d]
         L.or_face_grad.restype = None
@@ -120,7 +120,7 @@ def pipecg(s, b=None, x0=None, tol=1e-8, maxit=20000, rr_period=0, history=False
 
 
 def mixed_pipecg(s, b=None, x0=None, tol=1e-8, period=16, tau=0.0, restart=False,
-                 maxit=20000):
+                 maxit=20000, deflate=False):
     """FP32 pipelined Jacobi-PCG with FP64 residual replacement every `period`
     iterations (and when gamma dropped by tau^2, or convergence is predicted);
     restart=True turns the replacements into classic defect-correction restarts."""
@@ -130,7 +130,8 @@ def mixed_pipecg(s, b=None, x0=None, tol=1e-8, period=16, tau=0.0, restart=False
     it = ctypes.c_int(0)
     nrep = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
-    st = lib().or_mixed_pipecg(*args, _p(b), _p(x), tol, period, tau, int(bool(restart)), maxit,
+    st = lib().or_mixed_pipecg(*args, _p(b), _p(x), tol, period, tau, int(bool(restart)),
+                               int(bool(deflate)), maxit,
                                ctypes.byref(it), ctypes.byref(nrep), ctypes.byref(rr))
     return Result(x, st, it.value, rr.value, replacements=nrep.value)
 

@@ -359,11 +359,26 @@ static double dot32(int64_t n, const float *a, const float *b)
  * update), which keeps the Krylov convergence of the FP64 method.
  * iters counts float products A*m; replacements counts FP64 residuals,
  * including the initial one.  A non-positive delta on a fresh start
- * means the matrix is not SPD. */
+ * means the matrix is not SPD.
+ *
+ * deflate = 1 adds deflation of the constant vector W = 1 (deflated CG,
+ * Saad, Yeung, Erhel and Guyomarc'h, SIAM J. Sci. Comput. 21 (2000), with
+ * the Jacobi preconditioner, in pipelined form): with a1 = A W (FP64) and
+ * c = (W, a1), every replacement first applies the coarse correction
+ * x += (W, r64)/c W, r64 -= (W, r64)/c a1, and every step removes the
+ * A-component of W from the new direction, mu = (a1, u)/c:
+ *   p = u + beta p - mu W,  s = w + beta s - mu a1,
+ *   q = m + beta q - mu M^-1 a1,  z = n + beta z - mu A M^-1 a1,
+ * with denominator delta - beta*gamma/alpha_old - (a1, u)^2/c.  This takes
+ * the near-null constant mode of pure-Neumann (pressure) systems out of the
+ * float iteration, where the rounding of the float operator cannot resolve
+ * it.  W, a1, M^-1 a1 and A M^-1 a1 are formed in FP64 and rounded to
+ * float for the recurrences. */
 int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
                     const double *diag, const double *upper, const double *lower,
                     const double *b, double *x, double tol, int period, double tau,
-                    int restart, int maxit, int *iters, int *replacements, double *relres)
+                    int restart, int deflate, int maxit, int *iters, int *replacements,
+                    double *relres)
 {
     if (n < 0 || nf < 0 || maxit < 0 || period < 0 || !(tol >= 0.0) || !(tau >= 0.0))
         return OR_BAD_ARG;
@@ -378,12 +393,14 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
     }
     size_t nn = (size_t)(n > 0 ? n : 1), ff = (size_t)(nf > 0 ? nf : 1);
     double *r64 = (double *)malloc(sizeof(double) * nn);
+    double *a1 = (double *)malloc(sizeof(double) * nn);
+    double *t64 = (double *)malloc(sizeof(double) * nn);
     float *d32 = (float *)malloc(sizeof(float) * nn);
     float *u32 = (float *)malloc(sizeof(float) * ff);
     float *l32 = (float *)malloc(sizeof(float) * ff);
-    float *v[10] = {0};
-    int ok = r64 && d32 && u32 && l32;
-    for (int k = 0; k < 10 && ok; k++) {
+    float *v[14] = {0};
+    int ok = r64 && a1 && t64 && d32 && u32 && l32;
+    for (int k = 0; k < 14 && ok; k++) {
         v[k] = (float *)calloc(nn, sizeof(float));
         ok = v[k] != NULL;
     }
@@ -394,17 +411,41 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
     }
     float *r = v[0], *u = v[1], *w = v[2], *m = v[3], *nv = v[4];
     float *z = v[5], *q = v[6], *s = v[7], *p = v[8], *xc = v[9];
+    float *W32 = v[10], *a132 = v[11], *ma132 = v[12], *ama132 = v[13];
     for (int64_t i = 0; i < n; i++)
         d32[i] = (float)diag[i];
     for (int64_t f = 0; f < nf; f++) {
         u32[f] = (float)upper[f];
         l32[f] = (float)lower[f];
     }
+    double cW = 1.0;
+    if (deflate) {
+        for (int64_t i = 0; i < n; i++)
+            r64[i] = 1.0;                                   /* W = 1 */
+        or_spmv(n, nf, own, nbr, diag, upper, lower, r64, a1);   /* a1 = A W */
+        cW = 0.0;
+        for (int64_t i = 0; i < n; i++)
+            cW += a1[i];                                    /* (W, A W) */
+        if (!(cW > 0.0)) {
+            status = OR_NOT_SPD;
+            goto out;
+        }
+        for (int64_t i = 0; i < n; i++)
+            r64[i] = a1[i] / diag[i];                       /* M^-1 a1 */
+        or_spmv(n, nf, own, nbr, diag, upper, lower, r64, t64);  /* A M^-1 a1 */
+        for (int64_t i = 0; i < n; i++) {
+            W32[i] = 1.0f;
+            a132[i] = (float)a1[i];
+            ma132[i] = (float)r64[i];
+            ama132[i] = (float)t64[i];
+        }
+    }
     double sigma = 1.0, ratio = 1.0, gamma_old = 0.0, alpha_old = 0.0, gamma_ref = 0.0;
     int it = 0, since = 0, fresh = 1, force = 1, nrep = 0;
     for (;;) {
         double gamma = dot32(n, r, u);
         double delta = dot32(n, w, u);
+        double eps = deflate ? dot32(n, a132, u) : 0.0;
         double predicted = sqrt(ratio * gamma) * sigma / bnorm;
         int trigger = force || (period > 0 && since >= period)
                       || (tau > 0.0 && gamma <= tau * tau * gamma_ref)
@@ -415,6 +456,16 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
                 xc[i] = 0.0f;
             }
             residual(n, nf, own, nbr, diag, upper, lower, b, x, r64);
+            if (deflate) {
+                double a0 = 0.0;
+                for (int64_t i = 0; i < n; i++)
+                    a0 += r64[i];                           /* (W, r64) */
+                a0 /= cW;
+                for (int64_t i = 0; i < n; i++) {
+                    x[i] += a0;
+                    r64[i] -= a0 * a1[i];
+                }
+            }
             nrep++;
             double rn2 = dot(n, r64, r64);
             *relres = sqrt(rn2) / bnorm;
@@ -457,6 +508,7 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
             spmv32(n, nf, own, nbr, d32, u32, l32, q, z);
             gamma = dot32(n, r, u);
             delta = dot32(n, w, u);
+            eps = deflate ? dot32(n, a132, u) : 0.0;
             gamma_ref = gamma;
             since = 0;
             force = 0;
@@ -472,6 +524,8 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
             beta = gamma / gamma_old;
             denom = delta - beta * gamma / alpha_old;
         }
+        if (deflate)
+            denom -= eps * eps / cW;
         if (!(denom > 0.0) || !(gamma > 0.0)) {
             if (fresh) {
                 status = OR_NOT_SPD;
@@ -483,12 +537,18 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
         }
         fresh = 0;
         double alpha = gamma / denom;
-        float a = (float)alpha, bt = (float)beta;
+        float a = (float)alpha, bt = (float)beta, mu = (float)(eps / cW);
         for (int64_t i = 0; i < n; i++) {
             z[i] = nv[i] + bt * z[i];
             q[i] = m[i] + bt * q[i];
             s[i] = w[i] + bt * s[i];
             p[i] = u[i] + bt * p[i];
+            if (deflate) {
+                z[i] -= mu * ama132[i];
+                q[i] -= mu * ma132[i];
+                s[i] -= mu * a132[i];
+                p[i] -= mu * W32[i];
+            }
             xc[i] += a * p[i];
             r[i] -= a * s[i];
             u[i] -= a * q[i];
@@ -502,8 +562,8 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
     *iters = it;
     *replacements = nrep;
 out:
-    free(r64); free(d32); free(u32); free(l32);
-    for (int k = 0; k < 10; k++)
+    free(r64); free(a1); free(t64); free(d32); free(u32); free(l32);
+    for (int k = 0; k < 14; k++)
         free(v[k]);
     return status;
 }

@@ -98,7 +98,7 @@ struct ldu_matrix {
     float *val32;
     // work vectors
     double *v64[10];
-    float *v32[8];
+    float *v32[10];
     double *slots;          // [2][max_grid][kNumDots]
     int max_grid;
     unsigned *bar_count;
@@ -133,34 +133,33 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 
 // Grid-wide barrier for a cooperative launch.  `epoch` counts the barriers
 // this block has passed; arrivals accumulate in one counter that is never
-// reset during the launch.  Every spin is bounded: after timeout_ns the block
-// records kDevTimeout and all blocks leave at their next barrier.  Returns
-// false when the launch must stop.
+// reset during the launch.  Arrival is a release-add by thread 0 after the
+// block's __syncthreads (cumulative over the block's writes); the wait is an
+// acquire-load spin, so the block's later reads see every write made before
+// any block's arrival.  Every spin is bounded: after timeout_ns the block
+// records kDevTimeout and leaves; the others then time out at the next
+// barrier, which that block never reaches.  Returns false when the launch
+// must stop.
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_sync(const GridSync &g, unsigned &epoch) {
     __shared__ int s_fail;
     __syncthreads();
     epoch += 1;
     if (threadIdx.x == 0) {
         const unsigned target = epoch * gridDim.x;
-        __threadfence();
-        atomicAdd(g.count, 1u);
+        red_release_add_u32(g.count, 1u);
         int fail = 0;
         const unsigned long long t0 = global_ns();
         while ((int)(ld_acquire_u32(g.count) - target) < 0) {
-            if (*(volatile int *)g.err != 0) {
-                fail = 1;
-                break;
-            }
             if (global_ns() - t0 > g.timeout_ns) {
                 atomicCAS(g.err, 0, kDevTimeout);
                 fail = 1;
                 break;
             }
-            __nanosleep(40);
         }
-        __threadfence();
-        if (*(volatile int *)g.err != 0)
-            fail = 1;
         s_fail = fail;
     }
     __syncthreads();
@@ -202,25 +201,159 @@ __device__ __forceinline__ void block_sum_to_slot(double (&v)[K], double *slot) 
 }
 
 // After a barrier: every block sums the per-block slots in the same fixed
-// order, so all blocks hold bitwise-identical totals.
+// order (thread t takes slots t, t + blockDim, ...; then a fixed tree), so
+// all blocks hold bitwise-identical totals.  All slot loads of a thread are
+// independent, so the sum costs about one L2 round trip.
 template <int K>
 __device__ __forceinline__ void grid_total(const double *slots, double (&out)[K]) {
+    __shared__ double sm[32][K];
     __shared__ double res[K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp == 0) {
-        double t[K];
+    const int nwarps = blockDim.x >> 5;
+    double t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        t[k] = 0.0;
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x)
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            t[k] = 0.0;
-        for (int c = lane; c < (int)gridDim.x; c += 32)
+            t[k] += __ldcg(slots + (size_t)c * kNumDots + k);
+    warp_sum<K>(t);
+    if (lane == 0)
 #pragma unroll
-            for (int k = 0; k < K; ++k)
-                t[k] += __ldcg(slots + (size_t)c * kNumDots + k);
+        for (int k = 0; k < K; ++k)
+            sm[warp][k] = t[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            t[k] = lane < nwarps ? sm[lane][k] : 0.0;
         warp_sum<K>(t);
         if (lane == 0)
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 res[k] = t[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        out[k] = res[k];
+}
+
+// ---- float-pair ("double-float") sums ---------------------------------------
+// FP64 instructions are scarce on this GPU (a warp-wide FP64 add occupies the
+// pipe for on the order of a hundred cycles), so per-iteration reductions
+// carry each value as an unevaluated sum hi + lo of two floats, combined
+// with Knuth's TwoSum: about 48 significant bits, all in FP32 instructions.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const FF s = ff_two_sum(a.hi, b.hi);
+    const float e = s.lo + (a.lo + b.lo);
+    const float h = s.hi + e;
+    return {h, e - (h - s.hi)};
+}
+
+__device__ __forceinline__ FF ff_from_double(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ double ff_value(FF a) { return (double)a.hi + (double)a.lo; }
+
+// Compensated (Kahan) float accumulation: a thread sums its share of a dot
+// product in float with a running correction term, so the per-thread sum
+// keeps close to double accuracy without FP64 instructions in the sweep.
+struct KahanF {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ FF ff() const { return ff_two_sum(s, -c); }
+};
+
+template <int K>
+__device__ __forceinline__ void warp_sum_ff(FF (&v)[K]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            FF t;
+            t.hi = __shfl_down_sync(kFullMask, v[k].hi, o);
+            t.lo = __shfl_down_sync(kFullMask, v[k].lo, o);
+            v[k] = ff_add(v[k], t);
+        }
+}
+
+// Float-pair block sum into slot[0..K) (one float2 per value), fixed order.
+template <int K>
+__device__ __forceinline__ void block_sum_ff(FF (&v)[K], float2 *slot) {
+    __shared__ FF sm[32][K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    warp_sum_ff<K>(v);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            sm[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+        FF t[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            t[k] = lane < nwarps ? sm[lane][k] : FF{0.0f, 0.0f};
+        warp_sum_ff<K>(t);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                slot[k] = make_float2(t[k].hi, t[k].lo);
+    }
+}
+
+// Float-pair grid total after a barrier (same fixed order in every block).
+template <int K>
+__device__ __forceinline__ void grid_total_ff(const float2 *slots, double (&out)[K]) {
+    __shared__ FF sm[32][K];
+    __shared__ double res[K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    FF t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        t[k] = FF{0.0f, 0.0f};
+    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float2 v = __ldcg(slots + (size_t)c * kNumDots + k);
+            t[k] = ff_add(t[k], FF{v.x, v.y});
+        }
+    warp_sum_ff<K>(t);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            sm[warp][k] = t[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            t[k] = lane < nwarps ? sm[lane][k] : FF{0.0f, 0.0f};
+        warp_sum_ff<K>(t);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                res[k] = ff_value(t[k]);
     }
     __syncthreads();
 #pragma unroll

@@ -8,7 +8,7 @@
 // allocates the repacked matrix and work vectors.  This entry point takes
 // the caller's LDU arrays directly, repacks them and runs the same FP64
 // Jacobi-PCG kernel as pcg_solve, with every intermediate array in one
-// file-scope __device__ array of fixed size (kScratchBytes, about 8.9 MB)
+// file-scope __device__ array of fixed size (kScratchBytes, 8,130,816 bytes (7.75 MiB))
 // that each GPU loading the library holds until the process exits.
 //
 // The scratch is shared by all calls on a device and keeps whatever the last
@@ -54,9 +54,12 @@ constexpr size_t kOffDg = kOffIsd + align256(sizeof(double) * kMaxRows);
 constexpr size_t kOffVec = kOffDg + align256(sizeof(double) * kMaxRows);   // 5 FP64 vectors
 constexpr size_t kOffSlots = kOffVec + 5 * align256(sizeof(double) * kMaxRows);
 constexpr size_t kOffWords = kOffSlots + align256(sizeof(double) * 2 * kMaxGrid * kNumDots);
-// words: [0] barrier count, [64] barrier error, [128] flags, [192] slot total, [256..] SolveOut
+// words (byte offsets): 0 barrier count, 256 barrier error, 512 flags,
+// 768 slot total, 1024 SolveOut
 constexpr size_t kWordsBytes = 2048;
 constexpr size_t kScratchBytes = kOffWords + kWordsBytes;
+
+static_assert(kScratchBytes == 8130816, "the scratch size is stated in ldupcg.h");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -197,7 +200,7 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
                                                          val32);
     CK(cudaGetLastError());
 
-    const void *kern = (const void *)k_pcg64<4, 3>;
+    const void *kern = (const void *)k_pcg64<4, Batch<4>::pcg>;   // pcg_solve's kernel for C = 128
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNoallocBlock, 0));
     if (per_sm < 1)
@@ -227,13 +230,14 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     for (int k = 0; k < 10; ++k)
         P.v64[k] = k < 5 ? (double *)(base + kOffVec + (size_t)k * align256(sizeof(double) * kMaxRows))
                          : nullptr;
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 10; ++k)
         P.v32[k] = nullptr;
     P.tol = tol;
     P.maxit = maxit;
     P.rr_period = 0;
     P.tau = 0.0;
     P.restart = 0;
+    P.deflate = 0;
     P.fault_inject = 0;
     void *args[] = {&P};
     CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kNoallocBlock), args, 0, st));

@@ -270,7 +270,7 @@ int ldu_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *neigh
         CK(dev_alloc(&A->v64[k], A->n_pad, &b));
         CK(cudaMemsetAsync(A->v64[k], 0, sizeof(double) * (size_t)std::max<int64_t>(A->n_pad, 1), st));
     }
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 10; ++k) {
         CK(dev_alloc(&A->v32[k], A->n_pad, &b));
         CK(cudaMemsetAsync(A->v32[k], 0, sizeof(float) * (size_t)std::max<int64_t>(A->n_pad, 1), st));
     }

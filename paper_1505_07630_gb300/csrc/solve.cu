@@ -39,16 +39,15 @@ namespace {
 // ---------------------------------------------------------------------------
 // host side
 
-enum Kind { kPcg = 0, kPipe = 1, kMixed = 2 };
+enum Kind { kPcg = 0, kPipe = 1, kMixed = 2, kMixedDeflated = 3 };
 
 template <int R>
 const void *kernel_ptr(Kind k) {
-    constexpr int KB64 = R == 4 ? 3 : (R == 2 ? 6 : 6);
-    constexpr int KB32 = R == 4 ? 6 : 6;
     switch (k) {
-    case kPcg: return (const void *)k_pcg64<R, KB64>;
-    case kPipe: return (const void *)k_pipe64<R, KB64>;
-    default: return (const void *)k_mixed<R, KB32>;
+    case kPcg: return (const void *)k_pcg64<R, Batch<R>::pcg>;
+    case kPipe: return (const void *)k_pipe64<R, Batch<R>::pipe>;
+    case kMixed: return (const void *)k_mixed<R, Batch<R>::mixed, false>;
+    default: return (const void *)k_mixed<R, Batch<R>::mixed, true>;
     }
 }
 
@@ -78,7 +77,8 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     pcg_opts opt{};
     if (o)
         opt = *o;
-    if (opt.rr_period < 0 || opt.tau < 0.0 || opt.barrier_timeout_s < 0.0)
+    if (opt.rr_period < 0 || opt.tau < 0.0 || opt.barrier_timeout_s < 0.0 ||
+        (opt.deflate != 0 && opt.deflate != 1))
         return LDU_ERR_BAD_ARG;
     if (kind == kMixed && opt.rr_period == 0 && !o)
         opt.rr_period = 16;
@@ -93,7 +93,7 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
         A->last.status = LDU_OK;
         return LDU_OK;
     }
-    const void *kern = pick_kernel(A, kind);
+    const void *kern = pick_kernel(A, (kind == kMixed && opt.deflate) ? kMixedDeflated : kind);
     int grid = 0;
     int rc = grid_for(A, kern, A->block_threads, &grid);
     if (rc != LDU_OK)
@@ -110,13 +110,14 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     P.x = x;
     for (int k = 0; k < 10; ++k)
         P.v64[k] = A->v64[k];
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 10; ++k)
         P.v32[k] = A->v32[k];
     P.tol = tol;
     P.maxit = maxit;
     P.rr_period = opt.rr_period;
     P.tau = opt.tau;
     P.restart = opt.restart;
+    P.deflate = kind == kMixed ? opt.deflate : 0;
     P.fault_inject = opt.fault_inject;
     cudaError_t e;
     if ((e = cudaMemsetAsync(A->bar_count, 0, sizeof(unsigned) * 64, st)) != cudaSuccess)

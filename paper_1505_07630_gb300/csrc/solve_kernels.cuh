@@ -1,6 +1,15 @@
 // solve_kernels.cuh -- the persistent cooperative solver kernels (see
 // solve.cu for the algorithms) and their parameter block.  Included by the
 // .cu files that launch them; each gets its own copy (anonymous namespace).
+//
+// Control: the scalar recurrences (alpha, beta, stopping tests, replacement
+// triggers) run in thread 0 of every block, in FP64, on totals that are
+// bitwise identical in every block; thread 0 publishes its decisions in a
+// shared-memory block and the other threads read them after __syncthreads.
+// Per-iteration dot products are reduced as float pairs (FF); the rare
+// FP64 reductions (start-up, residual replacement) stay in double.  Tests
+// compare squared norms with precomputed squared thresholds, so an
+// iteration needs no square root.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,17 +25,18 @@ using namespace ldu;
 struct SolveParams {
     SellView A;
     GridSync sync;
-    double *slots;       // [2][gridDim.x][kNumDots]
+    double *slots;       // [2][gridDim.x][kNumDots]; FF sums use the same cells as float2
     SolveOut *out;
     const double *b;     // caller, n entries
     double *x;           // caller, n entries: x0 in, solution out
     double *v64[10];
-    float *v32[8];
+    float *v32[10];
     double tol;
     int maxit;
     int rr_period;
     double tau;
     int restart;
+    int deflate;
     int fault_inject;
 };
 
@@ -37,17 +47,47 @@ __device__ __forceinline__ const double *slots_all(const SolveParams &P, int par
     return P.slots + (size_t)parity * gridDim.x * kNumDots;
 }
 
-// Reduce K partials over the grid: block sums -> slot -> barrier -> totals.
+// Slots taken per batch by sell_accum for each solver and rows per lane R:
+// the largest batch that compiles without register spills at 128
+// registers per thread (two 256-thread blocks per SM).
+template <int R>
+struct Batch {
+    static constexpr int pcg = R == 4 ? 2 : 3;
+    static constexpr int pipe = R == 1 ? 3 : 1;
+    static constexpr int mixed = R == 4 ? 2 : (R == 2 ? 3 : 6);
+};
+
+// FP64 reduction of K partials: block sums -> slot -> barrier -> totals.
 // Returns false when the barrier failed (the kernel must return).
 template <int K>
-__device__ __forceinline__ bool reduce_grid(const SolveParams &P, double (&part)[K], double (&tot)[K],
-                                            unsigned &epoch, int &parity) {
+__device__ __forceinline__ bool reduce_d(const SolveParams &P, double (&part)[K], double (&tot)[K],
+                                         unsigned &epoch, int &parity) {
     block_sum_to_slot<K>(part, slot_of(P, parity));
     if (!grid_sync(P.sync, epoch))
         return false;
     grid_total<K>(slots_all(P, parity), tot);
     parity ^= 1;
     return true;
+}
+
+// The same with float-pair arithmetic (per-iteration dot products).
+template <int K>
+__device__ __forceinline__ bool reduce_f(const SolveParams &P, FF (&part)[K], double (&tot)[K],
+                                         unsigned &epoch, int &parity) {
+    block_sum_ff<K>(part, reinterpret_cast<float2 *>(slot_of(P, parity)));
+    if (!grid_sync(P.sync, epoch))
+        return false;
+    grid_total_ff<K>(reinterpret_cast<const float2 *>(slots_all(P, parity)), tot);
+    parity ^= 1;
+    return true;
+}
+
+// A power of two close to 1/x (1 for x == 0): scales FP64 partials into the
+// float range before a float-pair reduction, exactly.
+__device__ __forceinline__ double inv_pow2(double x) {
+    if (!(x > 0.0) || !isfinite(x))
+        return 1.0;
+    return ldexp(1.0, -ilogb(x));
 }
 
 #define LANE_ROWS                                             \
@@ -59,8 +99,8 @@ __device__ __forceinline__ bool reduce_grid(const SolveParams &P, double (&part)
 
 #define FOR_MY_SLICES(s) for (int s = range.begin + warp; s < range.end; s += nwarps)
 
-// pass 0 of every solver: bhat = b / sd, xhat = x0 * sd (rows < n), zero the
-// listed vectors; partial ||b||^2 in part[0]
+// pass 0 of every solver: bhat = b / sd, xhat = x0 * sd (rows < n); partial
+// ||b||^2 in part[0]
 template <int R>
 __device__ __forceinline__ void prep_pass(const SolveParams &P, double *bh, double *xh, double (&part)[1]) {
     LANE_ROWS;
@@ -112,8 +152,8 @@ __device__ __forceinline__ void zero_solution(const SolveParams &P) {
         P.x[r] = 0.0;
 }
 
-__device__ __forceinline__ void write_out(const SolveParams &P, int status, int iters, int reps, double relres,
-                          double bnorm) {
+__device__ __forceinline__ void write_out(const SolveParams &P, int status, int iters, int reps,
+                                          double relres, double bnorm) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.out->status = status;
         P.out->iters = iters;
@@ -125,8 +165,8 @@ __device__ __forceinline__ void write_out(const SolveParams &P, int status, int 
 
 // r = bhat - (I + Ahat_off) xhat (FP64); partials (r,r) and sum d r^2
 template <int R, int KB>
-__device__ __forceinline__ void residual64_pass(const SolveParams &P, const double *bh, const double *xh, double *r,
-                                double (&part)[2]) {
+__device__ __forceinline__ void residual64_pass(const SolveParams &P, const double *bh,
+                                                const double *xh, double *r, double (&part)[2]) {
     LANE_ROWS;
     const SellView &A = P.A;
     FOR_MY_SLICES(s) {
@@ -149,6 +189,11 @@ __device__ __forceinline__ void residual64_pass(const SolveParams &P, const doub
 // ============================================================================
 // Jacobi-PCG, FP64
 // v64: 0 xhat, 1 bhat, 2 r, 3 p, 4 q
+struct PcgCtl {
+    double alpha, beta;
+    int exit, check, truth;
+};
+
 template <int R, int KB>
 __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
     if (P.fault_inject && blockIdx.x == 0)
@@ -156,145 +201,180 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
     LANE_ROWS;
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *r = P.v64[2], *p = P.v64[3], *q = P.v64[4];
+    __shared__ PcgCtl ctl;
+    const bool t0 = threadIdx.x == 0;
     unsigned epoch = 0;
     int parity = 0;
 
     double b2[1] = {0.0}, t1[1];
     prep_pass<R>(P, bh, xh, b2);
     zero_rows<double, R>(P, p);   // the first p = r + 0 * p must not see stale values
-    if (!reduce_grid<1>(P, b2, t1, epoch, parity))
+    if (!reduce_d<1>(P, b2, t1, epoch, parity))
         return;
-    const double bnorm = sqrt(t1[0]);
-    if (bnorm == 0.0) {
+    const double bn2 = t1[0];
+    if (bn2 == 0.0) {
         zero_solution(P);
         write_out(P, kDevOk, 0, 0, 0.0, 0.0);
         return;
     }
+    const double thr2 = P.tol * P.tol * bn2;   // stop when sum d r^2 <= tol^2 ||b||^2
     double part[2] = {0.0, 0.0}, tot[2];
     residual64_pass<R, KB>(P, bh, xh, r, part);
-    if (!reduce_grid<2>(P, part, tot, epoch, parity))
+    if (!reduce_d<2>(P, part, tot, epoch, parity))
         return;
-    double gamma = tot[0];
-    double relres = sqrt(tot[1]) / bnorm;
+    // thread-0 state
+    double gamma = tot[0], rho = tot[1];
     int status = kDevNotConverged, it = 0, reps = 1;
-    bool truth = true;   // relres is of a freshly computed true residual
-    double beta = 0.0;
-    if (relres <= P.tol) {
-        status = kDevOk;
-    } else {
-        for (;;) {
-            // p = r + beta p
-            FOR_MY_SLICES(s) {
-                const int row0 = s * A.C + R * lane;
-                double rr[R], pp[R];
-                ld_rows<R>(r + row0, rr);
-                ld_rows<R>(p + row0, pp);
+    // float-pair sums carry (r,r)-sized values scaled by sg, d-weighted ones by sr
+    const double sg = inv_pow2(gamma), sr = inv_pow2(rho);
+    if (t0) {
+        ctl.exit = rho <= thr2;
+        ctl.beta = 0.0;
+        ctl.truth = 1;
+        if (ctl.exit)
+            status = kDevOk;
+    }
+    __syncthreads();
+    while (!ctl.exit) {
+        // p = r + beta p
+        const double beta = ctl.beta;
+        FOR_MY_SLICES(s) {
+            const int row0 = s * A.C + R * lane;
+            double rr[R], pp[R];
+            ld_rows<R>(r + row0, rr);
+            ld_rows<R>(p + row0, pp);
 #pragma unroll
-                for (int j = 0; j < R; ++j)
-                    pp[j] = fma(beta, pp[j], rr[j]);
-                st_rows<R>(p + row0, pp);
-            }
-            if (!grid_sync(P.sync, epoch))
-                return;
-            if (it >= P.maxit) {
-                status = kDevNotConverged;
-                break;
-            }
-            // q = Ahat p ; (p, q)
-            double pq[1] = {0.0}, tpq[1];
-            FOR_MY_SLICES(s) {
-                const int row0 = s * A.C + R * lane;
-                double acc[R];
-                ld_rows<R>(p + row0, acc);
-                double pp[R];
+            for (int j = 0; j < R; ++j)
+                pp[j] = fma(beta, pp[j], rr[j]);
+            st_rows<R>(p + row0, pp);
+        }
+        if (!grid_sync(P.sync, epoch))
+            return;
+        if (t0 && it >= P.maxit) {
+            ctl.exit = 1;
+            status = kDevNotConverged;
+        }
+        __syncthreads();
+        if (ctl.exit)
+            break;
+        // q = Ahat p ; (p, q)
+        double pq = 0.0;
+        FOR_MY_SLICES(s) {
+            const int row0 = s * A.C + R * lane;
+            double acc[R], pp[R];
+            ld_rows<R>(p + row0, acc);
 #pragma unroll
-                for (int j = 0; j < R; ++j)
-                    pp[j] = acc[j];
-                sell_accum<double, R, KB>(A, s, lane, p, acc);
+            for (int j = 0; j < R; ++j)
+                pp[j] = acc[j];
+            sell_accum<double, R, KB>(A, s, lane, p, acc);
 #pragma unroll
-                for (int j = 0; j < R; ++j)
-                    pq[0] = fma(pp[j], acc[j], pq[0]);
-                st_rows<R>(q + row0, acc);
-            }
-            if (!reduce_grid<1>(P, pq, tpq, epoch, parity))
-                return;
-            if (!(tpq[0] > 0.0)) {
+            for (int j = 0; j < R; ++j)
+                pq = fma(pp[j], acc[j], pq);
+            st_rows<R>(q + row0, acc);
+        }
+        FF fpq[1] = {ff_from_double(pq * sg)};
+        double tpq[1];
+        if (!reduce_f<1>(P, fpq, tpq, epoch, parity))
+            return;
+        if (t0) {
+            const double pqv = tpq[0] / sg;
+            if (!(pqv > 0.0)) {
                 status = kDevNotSpd;
-                break;
+                ctl.exit = 1;
+            } else {
+                ctl.alpha = gamma / pqv;
             }
-            const double alpha = gamma / tpq[0];
-            // x += alpha p ; r -= alpha q ; (r, r), sum d r^2
-            double pr[2] = {0.0, 0.0}, tr[2];
-            FOR_MY_SLICES(s) {
-                const int row0 = s * A.C + R * lane;
-                double xx[R], pp[R], rr[R], qq[R], dd[R];
-                ld_rows<R>(xh + row0, xx);
-                ld_rows<R>(p + row0, pp);
-                ld_rows<R>(r + row0, rr);
-                ld_rows<R>(q + row0, qq);
-                ld_rows<R>(A.dg + row0, dd);
+        }
+        __syncthreads();
+        if (ctl.exit)
+            break;
+        const double alpha = ctl.alpha;
+        // x += alpha p ; r -= alpha q ; (r, r), sum d r^2
+        double g0 = 0.0, g1 = 0.0;
+        FOR_MY_SLICES(s) {
+            const int row0 = s * A.C + R * lane;
+            double xx[R], pp[R], rr[R], qq[R], dd[R];
+            ld_rows<R>(xh + row0, xx);
+            ld_rows<R>(p + row0, pp);
+            ld_rows<R>(r + row0, rr);
+            ld_rows<R>(q + row0, qq);
+            ld_rows<R>(A.dg + row0, dd);
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    xx[j] = fma(alpha, pp[j], xx[j]);
-                    rr[j] = fma(-alpha, qq[j], rr[j]);
-                    pr[0] = fma(rr[j], rr[j], pr[0]);
-                    pr[1] = fma(dd[j] * rr[j], rr[j], pr[1]);
-                }
-                st_rows<R>(xh + row0, xx);
-                st_rows<R>(r + row0, rr);
+            for (int j = 0; j < R; ++j) {
+                xx[j] = fma(alpha, pp[j], xx[j]);
+                rr[j] = fma(-alpha, qq[j], rr[j]);
+                g0 = fma(rr[j], rr[j], g0);
+                g1 = fma(dd[j] * rr[j], rr[j], g1);
             }
-            if (!reduce_grid<2>(P, pr, tr, epoch, parity))
-                return;
+            st_rows<R>(xh + row0, xx);
+            st_rows<R>(r + row0, rr);
+        }
+        FF fr[2] = {ff_from_double(g0 * sg), ff_from_double(g1 * sr)};
+        double tr[2];
+        if (!reduce_f<2>(P, fr, tr, epoch, parity))
+            return;
+        if (t0) {
             ++it;
-            relres = sqrt(tr[1]) / bnorm;
-            truth = false;
-            double gamma_new = tr[0];
-            if (relres <= P.tol) {
-                // confirm with the true residual; restart the search if it disagrees
-                double pt[2] = {0.0, 0.0}, tt[2];
-                residual64_pass<R, KB>(P, bh, xh, r, pt);
-                if (!reduce_grid<2>(P, pt, tt, epoch, parity))
-                    return;
-                ++reps;
-                relres = sqrt(tt[1]) / bnorm;
-                truth = true;
-                if (relres <= P.tol) {
-                    status = kDevOk;
-                    break;
-                }
-                gamma = tt[0];
-                beta = 0.0;
-                continue;
+            ctl.truth = 0;
+            const double gamma_new = tr[0] / sg;
+            rho = tr[1] / sr;
+            if (rho <= thr2) {
+                ctl.check = 1;
+            } else {
+                ctl.check = 0;
+                ctl.beta = gamma_new / gamma;
+                gamma = gamma_new;
             }
-            beta = gamma_new / gamma;
-            gamma = gamma_new;
+        }
+        __syncthreads();
+        if (ctl.check) {
+            // confirm with the true residual; restart the search if it disagrees
+            double pt[2] = {0.0, 0.0}, tt[2];
+            residual64_pass<R, KB>(P, bh, xh, r, pt);
+            if (!reduce_d<2>(P, pt, tt, epoch, parity))
+                return;
+            if (t0) {
+                ++reps;
+                ctl.truth = 1;
+                rho = tt[1];
+                if (rho <= thr2) {
+                    status = kDevOk;
+                    ctl.exit = 1;
+                } else {
+                    gamma = tt[0];
+                    ctl.beta = 0.0;
+                }
+            }
+            __syncthreads();
         }
     }
-    if (!truth) {
+    if (!ctl.truth) {
         double pt[2] = {0.0, 0.0}, tt[2];
         residual64_pass<R, KB>(P, bh, xh, r, pt);
-        if (!reduce_grid<2>(P, pt, tt, epoch, parity))
+        if (!reduce_d<2>(P, pt, tt, epoch, parity))
             return;
-        ++reps;
-        relres = sqrt(tt[1]) / bnorm;
+        if (t0) {
+            ++reps;
+            rho = tt[1];
+        }
     }
     unscale_pass<R>(P, xh);
-    write_out(P, status, it, reps, relres, bnorm);
+    if (t0)
+        write_out(P, status, it, reps, sqrt(rho / bn2), sqrt(bn2));
 }
 
 // ============================================================================
 // pipelined PCG, FP64
 // v64: 0 xhat, 1 bhat, 2 r, 3 w(a), 4 w(b), 5 z, 6 s, 7 p
 template <int R, int KB>
-__device__ __forceinline__ bool pipe64_replace(const SolveParams &P, const double *w_cur_c, double (&tot)[3],
-                               unsigned &epoch, int &parity) {
+__device__ __forceinline__ bool pipe64_replace(const SolveParams &P, double *w, double (&tot)[3],
+                                               unsigned &epoch, int &parity) {
     LANE_ROWS;
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *r = P.v64[2];
-    double *w = const_cast<double *>(w_cur_c);
     double *z = P.v64[5], *sv = P.v64[6], *p = P.v64[7];
     // r = bhat - Ahat xhat
-    double d2[2] = {0.0, 0.0}, t2[2];
+    double d2[2] = {0.0, 0.0};
     residual64_pass<R, KB>(P, bh, xh, r, d2);
     if (!grid_sync(P.sync, epoch))
         return false;
@@ -328,10 +408,13 @@ __device__ __forceinline__ bool pipe64_replace(const SolveParams &P, const doubl
             part[2] = fma(dd[j] * rr[j], rr[j], part[2]);
         }
     }
-    (void)d2;
-    (void)t2;
-    return reduce_grid<3>(P, part, tot, epoch, parity);
+    return reduce_d<3>(P, part, tot, epoch, parity);
 }
+
+struct PipeCtl {
+    double alpha, beta;
+    int action;   // 0 step, 1 replace, 2 exit
+};
 
 template <int R, int KB>
 __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
@@ -340,8 +423,10 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
     LANE_ROWS;
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *r = P.v64[2];
-    double *wbuf[2] = {P.v64[3], P.v64[4]};
+    double *wa = P.v64[3], *wb = P.v64[4];
     double *z = P.v64[5], *sv = P.v64[6], *p = P.v64[7];
+    __shared__ PipeCtl ctl;
+    const bool t0 = threadIdx.x == 0;
     unsigned epoch = 0;
     int parity = 0, wc = 0;
 
@@ -350,71 +435,82 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
     zero_rows<double, R>(P, p);
     zero_rows<double, R>(P, z);
     zero_rows<double, R>(P, sv);
-    if (!reduce_grid<1>(P, b2, t1, epoch, parity))
+    if (!reduce_d<1>(P, b2, t1, epoch, parity))
         return;
-    const double bnorm = sqrt(t1[0]);
-    if (bnorm == 0.0) {
+    const double bn2 = t1[0];
+    if (bn2 == 0.0) {
         zero_solution(P);
         write_out(P, kDevOk, 0, 0, 0.0, 0.0);
         return;
     }
+    const double thr2 = P.tol * P.tol * bn2;
     double tot[3];
-    if (!pipe64_replace<R, KB>(P, wbuf[wc], tot, epoch, parity))
+    if (!pipe64_replace<R, KB>(P, wa, tot, epoch, parity))
         return;
+    // thread-0 state
     int reps = 1, it = 0, since = 0, status = kDevNotConverged;
     bool truth = true, fresh = true;
-    double gamma = tot[0], delta = tot[1], relres = sqrt(tot[2]) / bnorm;
+    double gamma = tot[0], delta = tot[1], rho = tot[2];
     double gamma_old = 0.0, alpha_old = 0.0;
+    const double sg = inv_pow2(gamma), sr = inv_pow2(rho);
     for (;;) {
-        const bool want = relres <= P.tol || (P.rr_period > 0 && since >= P.rr_period);
-        if (want && !truth) {
-            if (!pipe64_replace<R, KB>(P, wbuf[wc], tot, epoch, parity))
-                return;
-            ++reps;
-            since = 0;
-            truth = true;
-            gamma = tot[0];
-            delta = tot[1];
-            relres = sqrt(tot[2]) / bnorm;
-        }
-        if (truth && relres <= P.tol) {
-            status = kDevOk;
-            break;
-        }
-        if (it >= P.maxit) {
-            status = kDevNotConverged;
-            break;
-        }
-        double beta, denom;
-        if (fresh) {
-            beta = 0.0;
-            denom = delta;
-        } else {
-            beta = gamma / gamma_old;
-            denom = delta - beta * gamma / alpha_old;
-        }
-        if (!(denom > 0.0) || !(gamma > 0.0)) {
-            if (fresh) {
-                status = kDevNotSpd;
-                break;
+        if (t0) {
+            const bool want = rho <= thr2 || (P.rr_period > 0 && since >= P.rr_period);
+            if (want && !truth) {
+                ctl.action = 1;
+            } else if (truth && rho <= thr2) {
+                status = kDevOk;
+                ctl.action = 2;
+            } else if (it >= P.maxit) {
+                status = kDevNotConverged;
+                ctl.action = 2;
+            } else {
+                double beta, denom;
+                if (fresh) {
+                    beta = 0.0;
+                    denom = delta;
+                } else {
+                    beta = gamma / gamma_old;
+                    denom = delta - beta * gamma / alpha_old;
+                }
+                if (!(denom > 0.0) || !(gamma > 0.0)) {
+                    if (fresh) {
+                        status = kDevNotSpd;
+                        ctl.action = 2;
+                    } else {
+                        // rounding drift: replace from the true residual and restart
+                        fresh = true;
+                        ctl.action = 1;
+                    }
+                } else {
+                    fresh = false;
+                    ctl.action = 0;
+                    ctl.beta = beta;
+                    ctl.alpha = gamma / denom;
+                }
             }
-            // rounding drift: replace from the true residual and restart
-            if (!pipe64_replace<R, KB>(P, wbuf[wc], tot, epoch, parity))
+        }
+        __syncthreads();
+        const int action = ctl.action;
+        if (action == 2)
+            break;
+        double *w = wc ? wb : wa;
+        if (action == 1) {
+            if (!pipe64_replace<R, KB>(P, w, tot, epoch, parity))
                 return;
-            ++reps;
-            since = 0;
-            truth = true;
-            fresh = true;
-            gamma = tot[0];
-            delta = tot[1];
-            relres = sqrt(tot[2]) / bnorm;
+            if (t0) {
+                ++reps;
+                since = 0;
+                truth = true;
+                gamma = tot[0];
+                delta = tot[1];
+                rho = tot[2];
+            }
             continue;
         }
-        fresh = false;
-        const double alpha = gamma / denom;
-        const double *w = wbuf[wc];
-        double *wn = wbuf[wc ^ 1];
-        double part[3] = {0.0, 0.0, 0.0};
+        const double alpha = ctl.alpha, beta = ctl.beta;
+        double *wn = wc ? wa : wb;
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
         FOR_MY_SLICES(s) {
             const int row0 = s * A.C + R * lane;
             double nn[R], ww[R];
@@ -438,9 +534,9 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
                 xx[j] = fma(alpha, pp[j], xx[j]);
                 rr[j] = fma(-alpha, ss[j], rr[j]);
                 ww[j] = fma(-alpha, zz[j], ww[j]);
-                part[0] = fma(rr[j], rr[j], part[0]);
-                part[1] = fma(ww[j], rr[j], part[1]);
-                part[2] = fma(dd[j] * rr[j], rr[j], part[2]);
+                g0 = fma(rr[j], rr[j], g0);
+                g1 = fma(ww[j], rr[j], g1);
+                g2 = fma(dd[j] * rr[j], rr[j], g2);
             }
             st_rows<R>(z + row0, zz);
             st_rows<R>(sv + row0, ss);
@@ -449,44 +545,75 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
             st_rows<R>(r + row0, rr);
             st_rows<R>(wn + row0, ww);
         }
-        if (!reduce_grid<3>(P, part, tot, epoch, parity))
+        FF fp[3] = {ff_from_double(g0 * sg), ff_from_double(g1 * sg), ff_from_double(g2 * sr)};
+        double tp[3];
+        if (!reduce_f<3>(P, fp, tp, epoch, parity))
             return;
         wc ^= 1;
-        gamma_old = gamma;
-        alpha_old = alpha;
-        gamma = tot[0];
-        delta = tot[1];
-        relres = sqrt(tot[2]) / bnorm;
-        truth = false;
-        ++it;
-        ++since;
+        if (t0) {
+            gamma_old = gamma;
+            alpha_old = alpha;
+            gamma = tp[0] / sg;
+            delta = tp[1] / sg;
+            rho = tp[2] / sr;
+            truth = false;
+            ++it;
+            ++since;
+        }
     }
-    if (!truth) {
+    __shared__ int s_need;   // truth is thread-0 state: broadcast the decision
+    if (t0)
+        s_need = !truth;
+    __syncthreads();
+    if (s_need) {
         double pt[2] = {0.0, 0.0}, tt[2];
         residual64_pass<R, KB>(P, bh, xh, r, pt);
-        if (!reduce_grid<2>(P, pt, tt, epoch, parity))
+        if (!reduce_d<2>(P, pt, tt, epoch, parity))
             return;
-        ++reps;
-        relres = sqrt(tt[1]) / bnorm;
+        if (t0) {
+            ++reps;
+            rho = tt[1];
+        }
     }
     unscale_pass<R>(P, xh);
-    write_out(P, status, it, reps, relres, bnorm);
+    if (t0)
+        write_out(P, status, it, reps, sqrt(rho / bn2), sqrt(bn2));
 }
 
 // ============================================================================
 // mixed precision: float pipelined recurrences, FP64 solution and residual
-// v64: 0 xhat, 1 bhat
-// v32: 0 xc, 1 r, 2 w(a), 3 w(b), 4 z, 5 s, 6 p
-template <int R, int KB>
+// v64: 0 xhat, 1 bhat, 2 rt (FP64 residual, deflation only), 3 w0, 4 q0
+// v32: 0 xc, 1 r, 2 w(a), 3 w(b), 4 z, 5 s, 6 p, 7 w0f, 8 q0f, 9 t0f
+//
+// Deflation (optional) of the constant vector: in the scaled space it is
+// w0 = D^1/2 1 / ||D^1/2 1||, with q0 = Ahat w0, t0 = Ahat q0 and
+// c = (w0, q0), all formed in FP64 at the start of the solve.
+struct MixedCtl {
+    double sigma;
+    float a, bt, mu, f, pf;
+    int action;   // 0 step, 1 replace, 2 exit
+};
+
+// The scalar state of the recurrences, kept by thread 0 in shared memory so
+// that it occupies no registers in the other threads.
+struct MixedState {
+    double sigma, ratio, gamma, delta, eps, gamma_old, alpha_old, gamma_ref, rho;
+    int it, since, reps, status, fresh, force;
+};
+
+template <int R, int KB, bool DEFL>
 __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
     if (P.fault_inject && blockIdx.x == 0)
         return;
     LANE_ROWS;
     const SellView &A = P.A;
-    double *xh = P.v64[0], *bh = P.v64[1];
-    float *xc = P.v32[0], *r = P.v32[1];
-    float *wbuf[2] = {P.v32[2], P.v32[3]};
+    double *xh = P.v64[0], *bh = P.v64[1], *rt = P.v64[2], *w0 = P.v64[3], *q0 = P.v64[4];
+    float *xc = P.v32[0], *r = P.v32[1], *wa = P.v32[2], *wb = P.v32[3];
     float *z = P.v32[4], *sv = P.v32[5], *p = P.v32[6];
+    float *w0f = P.v32[7], *q0f = P.v32[8], *t0f = P.v32[9];
+    constexpr bool defl = DEFL;   // a separate instantiation keeps the plain loop lean
+    __shared__ MixedCtl ctl;
+    const bool t0 = threadIdx.x == 0;
     unsigned epoch = 0;
     int parity = 0, wc = 0;
 
@@ -496,24 +623,103 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
     zero_rows<float, R>(P, p);
     zero_rows<float, R>(P, z);
     zero_rows<float, R>(P, sv);
-    if (!reduce_grid<1>(P, b2, t1, epoch, parity))
+    if (!reduce_d<1>(P, b2, t1, epoch, parity))
         return;
-    const double bnorm = sqrt(t1[0]);
-    if (bnorm == 0.0) {
+    const double bn2 = t1[0];
+    if (bn2 == 0.0) {
         zero_solution(P);
         write_out(P, kDevOk, 0, 0, 0.0, 0.0);
         return;
     }
-    double sigma = 1.0, ratio = 1.0, gamma = 0.0, delta = 0.0, gamma_old = 0.0, alpha_old = 0.0;
-    double gamma_ref = 0.0, relres = 1.0;
-    int it = 0, since = 0, reps = 0, status = kDevNotConverged;
-    bool fresh = true, force = true;
+    const double thr2 = P.tol * P.tol * bn2;
+    double cW = 1.0;   // (w0, q0)
+    if (defl) {
+        // ||D^1/2 1||^2 = sum d
+        double pd[1] = {0.0}, td[1];
+        FOR_MY_SLICES(s) {
+            const int row0 = s * A.C + R * lane;
+            double dd[R];
+            ld_rows<R>(A.dg + row0, dd);
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                pd[0] += dd[j];
+        }
+        if (!reduce_d<1>(P, pd, td, epoch, parity))
+            return;
+        const double inv_norm = 1.0 / sqrt(td[0]);
+        FOR_MY_SLICES(s) {
+            const int row0 = s * A.C + R * lane;
+            double ss[R];
+            float sf[R];
+            ld_rows<R>(A.sd + row0, ss);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                ss[j] = (row0 + j < A.n) ? ss[j] * inv_norm : 0.0;
+                sf[j] = (float)ss[j];
+            }
+            st_rows<R>(w0 + row0, ss);
+            st_rows<R>(w0f + row0, sf);
+        }
+        if (!grid_sync(P.sync, epoch))
+            return;
+        double pc[1] = {0.0}, tc[1];
+        FOR_MY_SLICES(s) {
+            const int row0 = s * A.C + R * lane;
+            double acc[R], ww[R];
+            float qf[R];
+            ld_rows<R>(w0 + row0, acc);
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                ww[j] = acc[j];
+            sell_accum<double, R, KB>(A, s, lane, w0, acc);
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                pc[0] = fma(ww[j], acc[j], pc[0]);
+                qf[j] = (float)acc[j];
+            }
+            st_rows<R>(q0 + row0, acc);
+            st_rows<R>(q0f + row0, qf);
+        }
+        if (!reduce_d<1>(P, pc, tc, epoch, parity))
+            return;
+        cW = tc[0];
+        FOR_MY_SLICES(s) {
+            const int row0 = s * A.C + R * lane;
+            double acc[R];
+            float tf[R];
+            ld_rows<R>(q0 + row0, acc);
+            sell_accum<double, R, KB>(A, s, lane, q0, acc);
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                tf[j] = (float)acc[j];
+            st_rows<R>(t0f + row0, tf);
+        }
+        if (!grid_sync(P.sync, epoch))
+            return;
+    }
+    __shared__ MixedState S;   // thread 0 only
+    if (t0) {
+        S.sigma = 1.0;
+        S.ratio = 1.0;
+        S.gamma = S.delta = S.eps = 0.0;
+        S.gamma_old = S.alpha_old = S.gamma_ref = 0.0;
+        S.rho = bn2;
+        S.it = S.since = S.reps = 0;
+        S.status = kDevNotConverged;
+        S.fresh = 1;
+        S.force = 1;
+        ctl.sigma = 1.0;
+    }
     for (;;) {
-        const double predicted = sqrt(ratio * gamma) * sigma / bnorm;
-        const bool trigger = force || (P.rr_period > 0 && since >= P.rr_period) ||
-                             (P.tau > 0.0 && gamma <= P.tau * P.tau * gamma_ref) ||
-                             predicted <= P.tol || it >= P.maxit;
-        if (trigger) {
+        if (t0) {
+            const bool trigger = S.force || (P.rr_period > 0 && S.since >= P.rr_period) ||
+                                 (P.tau > 0.0 && S.gamma <= P.tau * P.tau * S.gamma_ref) ||
+                                 S.ratio * S.gamma * S.sigma * S.sigma <= thr2 || S.it >= P.maxit;
+            ctl.action = trigger ? 1 : 0;
+        }
+        __syncthreads();
+        if (ctl.action == 1) {
+            const double sig = ctl.sigma;
             // U1: fold the float correction into the FP64 solution
             FOR_MY_SLICES(s) {
                 const int row0 = s * A.C + R * lane;
@@ -523,7 +729,7 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                 ld_rows<R>(xc + row0, cc);
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    xx[j] = fma(sigma, (double)cc[j], xx[j]);
+                    xx[j] = fma(sig, (double)cc[j], xx[j]);
                     zr[j] = 0.0f;
                 }
                 st_rows<R>(xh + row0, xx);
@@ -531,53 +737,103 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             }
             if (!grid_sync(P.sync, epoch))
                 return;
-            // U2: FP64 true residual, stored in float in units of the old sigma
-            const double inv_sigma = 1.0 / sigma;   // power of two: exact
+            // U2: FP64 true residual (deflated by the coarse correction), stored
+            // in float in units of the current sigma
+            const double inv_sigma = 1.0 / sig;   // power of two: exact
             double part[2] = {0.0, 0.0}, tot[2];
-            FOR_MY_SLICES(s) {
-                const int row0 = s * A.C + R * lane;
-                double acc[R], bb[R], dd[R];
-                ld_rows<R>(xh + row0, acc);
-                sell_accum<double, R, KB>(A, s, lane, xh, acc);
-                ld_rows<R>(bh + row0, bb);
-                ld_rows<R>(A.dg + row0, dd);
-                float rf[R];
+            if (!defl) {
+                FOR_MY_SLICES(s) {
+                    const int row0 = s * A.C + R * lane;
+                    double acc[R], bb[R], dd[R];
+                    ld_rows<R>(xh + row0, acc);
+                    sell_accum<double, R, KB>(A, s, lane, xh, acc);
+                    ld_rows<R>(bh + row0, bb);
+                    ld_rows<R>(A.dg + row0, dd);
+                    float rf[R];
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    const double rj = bb[j] - acc[j];
-                    part[0] = fma(rj, rj, part[0]);
-                    part[1] = fma(dd[j] * rj, rj, part[1]);
-                    rf[j] = (float)(rj * inv_sigma);
+                    for (int j = 0; j < R; ++j) {
+                        const double rj = bb[j] - acc[j];
+                        part[0] = fma(rj, rj, part[0]);
+                        part[1] = fma(dd[j] * rj, rj, part[1]);
+                        rf[j] = (float)(rj * inv_sigma);
+                    }
+                    st_rows<R>(r + row0, rf);
                 }
-                st_rows<R>(r + row0, rf);
+            } else {
+                double pw[1] = {0.0}, tw[1];
+                FOR_MY_SLICES(s) {
+                    const int row0 = s * A.C + R * lane;
+                    double acc[R], bb[R], ww[R];
+                    ld_rows<R>(xh + row0, acc);
+                    sell_accum<double, R, KB>(A, s, lane, xh, acc);
+                    ld_rows<R>(bh + row0, bb);
+                    ld_rows<R>(w0 + row0, ww);
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        acc[j] = bb[j] - acc[j];
+                        pw[0] = fma(ww[j], acc[j], pw[0]);
+                    }
+                    st_rows<R>(rt + row0, acc);
+                }
+                if (!reduce_d<1>(P, pw, tw, epoch, parity))
+                    return;
+                const double a0 = tw[0] / cW;   // every thread: same value, a few FP64 ops once
+                // U2b: x += a0 w0 ; r -= a0 q0 (own rows only)
+                FOR_MY_SLICES(s) {
+                    const int row0 = s * A.C + R * lane;
+                    double xx[R], rr[R], ww[R], qq[R], dd[R];
+                    float rf[R];
+                    ld_rows<R>(xh + row0, xx);
+                    ld_rows<R>(rt + row0, rr);
+                    ld_rows<R>(w0 + row0, ww);
+                    ld_rows<R>(q0 + row0, qq);
+                    ld_rows<R>(A.dg + row0, dd);
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        xx[j] = fma(a0, ww[j], xx[j]);
+                        const double rj = fma(-a0, qq[j], rr[j]);
+                        part[0] = fma(rj, rj, part[0]);
+                        part[1] = fma(dd[j] * rj, rj, part[1]);
+                        rf[j] = (float)(rj * inv_sigma);
+                    }
+                    st_rows<R>(xh + row0, xx);
+                    st_rows<R>(r + row0, rf);
+                }
             }
-            if (!reduce_grid<2>(P, part, tot, epoch, parity))
+            if (!reduce_d<2>(P, part, tot, epoch, parity))
                 return;
-            ++reps;
-            relres = sqrt(tot[1]) / bnorm;
-            if (relres <= P.tol) {
-                status = kDevOk;
-                break;
+            if (t0) {
+                ++S.reps;
+                S.rho = tot[1];
+                if (S.rho <= thr2) {
+                    S.status = kDevOk;
+                    ctl.action = 2;
+                } else if (S.it >= P.maxit) {
+                    S.status = kDevNotConverged;
+                    ctl.action = 2;
+                } else if (!(tot[0] > 0.0)) {
+                    S.status = kDevNotSpd;
+                    ctl.action = 2;
+                } else {
+                    S.ratio = tot[1] / tot[0];
+                    const double sigma_new = exp2(rint(log2(sqrt(tot[0]))));
+                    const float f = (float)(S.sigma / sigma_new);
+                    ctl.f = f;
+                    ctl.pf = P.restart ? 0.0f : f;
+                    if (P.restart)
+                        S.fresh = 1;
+                    else
+                        S.gamma_old *= (double)f * (double)f;
+                    S.sigma = sigma_new;
+                    ctl.sigma = sigma_new;
+                }
             }
-            if (it >= P.maxit) {
-                status = kDevNotConverged;
+            __syncthreads();
+            if (ctl.action == 2)
                 break;
-            }
-            if (!(tot[0] > 0.0)) {
-                status = kDevNotSpd;
-                break;
-            }
-            ratio = tot[1] / tot[0];
-            const double sigma_new = exp2(rint(log2(sqrt(tot[0]))));
-            const float f = (float)(sigma / sigma_new);
-            const float pf = P.restart ? 0.0f : f;
-            if (P.restart)
-                fresh = true;
-            else
-                gamma_old *= (double)f * (double)f;
-            sigma = sigma_new;
+            const float f = ctl.f, pf = ctl.pf;
             // U3: w = f (Ahat r) ; s = pf (Ahat p)
-            float *w = wbuf[wc];
+            float *w = wc ? wb : wa;
             FOR_MY_SLICES(s) {
                 const int row0 = s * A.C + R * lane;
                 float aw[R], as[R];
@@ -594,61 +850,89 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             }
             if (!grid_sync(P.sync, epoch))
                 return;
-            // U4: z = Ahat s ; r *= f ; p *= pf ; gamma = (r,r), delta = (w,r)
-            double pd[2] = {0.0, 0.0}, td[2];
+            // U4: z = Ahat s ; r *= f ; p *= pf ; gamma, delta (, eps)
+            KahanF g0, g1, g2;
             FOR_MY_SLICES(s) {
                 const int row0 = s * A.C + R * lane;
-                float az[R], rr[R], pp[R], ww[R];
+                float az[R], rr[R], pp[R], ww[R], qq[R];
                 ld_rows<R>(sv + row0, az);
                 sell_accum<float, R, KB>(A, s, lane, sv, az);
                 st_rows<R>(z + row0, az);
                 ld_rows<R>(r + row0, rr);
                 ld_rows<R>(p + row0, pp);
                 ld_rows<R>(w + row0, ww);
-                float g0 = 0.0f, g1 = 0.0f;
+                if (defl)
+                    ld_rows<R>(q0f + row0, qq);
+                float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
                     rr[j] *= f;
                     pp[j] *= pf;
-                    g0 = fmaf(rr[j], rr[j], g0);
-                    g1 = fmaf(ww[j], rr[j], g1);
+                    e0 = fmaf(rr[j], rr[j], e0);
+                    e1 = fmaf(ww[j], rr[j], e1);
+                    if (defl)
+                        e2 = fmaf(qq[j], rr[j], e2);
                 }
-                pd[0] += (double)g0;
-                pd[1] += (double)g1;
+                g0.add(e0);
+                g1.add(e1);
+                g2.add(e2);
                 st_rows<R>(r + row0, rr);
                 st_rows<R>(p + row0, pp);
             }
-            if (!reduce_grid<2>(P, pd, td, epoch, parity))
+            FF fd[3] = {g0.ff(), g1.ff(), g2.ff()};
+            double td[3];
+            if (!reduce_f<3>(P, fd, td, epoch, parity))
                 return;
-            gamma = td[0];
-            delta = td[1];
-            gamma_ref = gamma;
-            since = 0;
-            force = false;
-        }
-        double beta, denom;
-        if (fresh) {
-            beta = 0.0;
-            denom = delta;
-        } else {
-            beta = gamma / gamma_old;
-            denom = delta - beta * gamma / alpha_old;
-        }
-        if (!(denom > 0.0) || !(gamma > 0.0)) {
-            if (fresh) {
-                status = kDevNotSpd;
-                break;
+            if (t0) {
+                S.gamma = td[0];
+                S.delta = td[1];
+                S.eps = td[2];
+                S.gamma_ref = td[0];
+                S.since = 0;
+                S.force = 0;
             }
-            fresh = true;
-            force = true;
-            continue;
         }
-        fresh = false;
-        const double alpha = gamma / denom;
-        const float a = (float)alpha, bt = (float)beta;
-        const float *w = wbuf[wc];
-        float *wn = wbuf[wc ^ 1];
-        double part[2] = {0.0, 0.0}, tot[2];
+        if (t0) {
+            const double gamma = S.gamma;
+            double beta, denom;
+            if (S.fresh) {
+                beta = 0.0;
+                denom = S.delta;
+            } else {
+                beta = gamma / S.gamma_old;
+                denom = S.delta - beta * gamma / S.alpha_old;
+            }
+            if (defl)
+                denom -= S.eps * S.eps / cW;
+            if (!(denom > 0.0) || !(gamma > 0.0)) {
+                if (S.fresh) {
+                    S.status = kDevNotSpd;
+                    ctl.action = 2;
+                } else {
+                    S.fresh = 1;
+                    S.force = 1;
+                    ctl.action = 1;   // replace, then restart
+                }
+            } else {
+                S.fresh = 0;
+                const double alpha = gamma / denom;
+                ctl.action = 0;
+                ctl.a = (float)alpha;
+                ctl.bt = (float)beta;
+                ctl.mu = defl ? (float)(S.eps / cW) : 0.0f;
+                S.gamma_old = gamma;
+                S.alpha_old = alpha;
+            }
+        }
+        __syncthreads();
+        if (ctl.action == 2)
+            break;
+        if (ctl.action == 1)
+            continue;
+        const float a = ctl.a, bt = ctl.bt, mu = ctl.mu;
+        const float *w = wc ? wb : wa;
+        float *wn = wc ? wa : wb;
+        KahanF g0, g1, g2;   // per-thread partial dots, compensated
         FOR_MY_SLICES(s) {
             const int row0 = s * A.C + R * lane;
             float nn[R], ww[R];
@@ -663,20 +947,40 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             ld_rows<R>(p + row0, pp);
             ld_rows<R>(xc + row0, xx);
             ld_rows<R>(r + row0, rr);
-            float g0 = 0.0f, g1 = 0.0f;
+            float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
+            if (defl) {
+                float dw[R], dq[R], dt[R];
+                ld_rows<R>(w0f + row0, dw);
+                ld_rows<R>(q0f + row0, dq);
+                ld_rows<R>(t0f + row0, dt);
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                zz[j] = fmaf(bt, zz[j], nn[j]);
-                ss[j] = fmaf(bt, ss[j], ww[j]);
-                pp[j] = fmaf(bt, pp[j], rr[j]);
-                xx[j] = fmaf(a, pp[j], xx[j]);
-                rr[j] = fmaf(-a, ss[j], rr[j]);
-                ww[j] = fmaf(-a, zz[j], ww[j]);
-                g0 = fmaf(rr[j], rr[j], g0);
-                g1 = fmaf(ww[j], rr[j], g1);
+                for (int j = 0; j < R; ++j) {
+                    zz[j] = fmaf(-mu, dt[j], fmaf(bt, zz[j], nn[j]));
+                    ss[j] = fmaf(-mu, dq[j], fmaf(bt, ss[j], ww[j]));
+                    pp[j] = fmaf(-mu, dw[j], fmaf(bt, pp[j], rr[j]));
+                    xx[j] = fmaf(a, pp[j], xx[j]);
+                    rr[j] = fmaf(-a, ss[j], rr[j]);
+                    ww[j] = fmaf(-a, zz[j], ww[j]);
+                    e0 = fmaf(rr[j], rr[j], e0);
+                    e1 = fmaf(ww[j], rr[j], e1);
+                    e2 = fmaf(dq[j], rr[j], e2);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    zz[j] = fmaf(bt, zz[j], nn[j]);
+                    ss[j] = fmaf(bt, ss[j], ww[j]);
+                    pp[j] = fmaf(bt, pp[j], rr[j]);
+                    xx[j] = fmaf(a, pp[j], xx[j]);
+                    rr[j] = fmaf(-a, ss[j], rr[j]);
+                    ww[j] = fmaf(-a, zz[j], ww[j]);
+                    e0 = fmaf(rr[j], rr[j], e0);
+                    e1 = fmaf(ww[j], rr[j], e1);
+                }
             }
-            part[0] += (double)g0;
-            part[1] += (double)g1;
+            g0.add(e0);
+            g1.add(e1);
+            g2.add(e2);
             st_rows<R>(z + row0, zz);
             st_rows<R>(sv + row0, ss);
             st_rows<R>(p + row0, pp);
@@ -684,18 +988,22 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             st_rows<R>(r + row0, rr);
             st_rows<R>(wn + row0, ww);
         }
-        if (!reduce_grid<2>(P, part, tot, epoch, parity))
+        FF fp[3] = {g0.ff(), g1.ff(), g2.ff()};
+        double tp[3];
+        if (!reduce_f<3>(P, fp, tp, epoch, parity))
             return;
         wc ^= 1;
-        gamma_old = gamma;
-        alpha_old = alpha;
-        gamma = tot[0];
-        delta = tot[1];
-        ++it;
-        ++since;
+        if (t0) {
+            S.gamma = tp[0];
+            S.delta = tp[1];
+            S.eps = tp[2];
+            ++S.it;
+            ++S.since;
+        }
     }
     unscale_pass<R>(P, xh);
-    write_out(P, status, it, reps, relres, bnorm);
+    if (t0)
+        write_out(P, S.status, S.it, S.reps, sqrt(S.rho / bn2), sqrt(bn2));
 }
 
 }  // namespace

@@ -34,7 +34,8 @@ class LduOpts(ctypes.Structure):
 
 class PcgOpts(ctypes.Structure):
     _fields_ = [("rr_period", ctypes.c_int), ("tau", ctypes.c_double), ("restart", ctypes.c_int),
-                ("barrier_timeout_s", ctypes.c_double), ("fault_inject", ctypes.c_int)]
+                ("barrier_timeout_s", ctypes.c_double), ("fault_inject", ctypes.c_int),
+                ("deflate", ctypes.c_int)]
 
 
 class LduSolveStats(ctypes.Structure):
@@ -219,13 +220,14 @@ def pcg_solve(A, b, x=None, tol=1e-8, maxit=20000, stream=None, check=True):
 
 
 def pipecg_solve(A, b, x=None, tol=1e-8, maxit=20000, precision="fp64", rr_period=0, tau=0.0,
-                 restart=False, barrier_timeout_s=0.0, fault_inject=0, stream=None, check=True):
+                 restart=False, deflate=False, barrier_timeout_s=0.0, fault_inject=0, stream=None,
+                 check=True):
     """Pipelined Jacobi-PCG (precision 'fp64' or 'mixed').
     Returns (x, status, iters, relres)."""
     if x is None:
         x = torch.zeros(A.n, dtype=torch.float64, device=b.device)
     opts = PcgOpts(int(rr_period), float(tau), int(bool(restart)), float(barrier_timeout_s),
-                   int(fault_inject))
+                   int(fault_inject), int(bool(deflate)))
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
     st = lib().pipecg_solve(A.handle, _dev(b, torch.float64, A.n, "b"),

@@ -140,13 +140,15 @@ def test_pipecg_fp64_parity(pkg, oracle_mod, case):
 
 
 @pytest.mark.parametrize("case", list(SOLVE_CASES))
-@pytest.mark.parametrize("mode", [dict(rr_period=16), dict(rr_period=0, tau=1e-3, restart=True)])
+@pytest.mark.parametrize("mode", [dict(rr_period=16), dict(rr_period=0, tau=1e-3, restart=True),
+                                  dict(rr_period=16, deflate=True)])
 def test_mixed_parity(pkg, oracle_mod, case, mode):
     s = SOLVE_CASES[case]()
     A = pkg.from_system(s)
     b = cuda(s.b)
     ref = oracle_mod.mixed_pipecg(s, tol=1e-8, period=mode["rr_period"],
-                                  tau=mode.get("tau", 0.0), restart=mode.get("restart", False))
+                                  tau=mode.get("tau", 0.0), restart=mode.get("restart", False),
+                                  deflate=mode.get("deflate", False))
     x, st, it, rr = pkg.pipecg_solve(A, b, tol=1e-8, precision="mixed", **mode)
     xh = x.cpu().numpy()
     true_rr = oracle_mod.true_relres(s, xh)

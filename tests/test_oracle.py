@@ -152,7 +152,8 @@ def test_pipecg_matches_lu(oracle_mod, make):
 
 
 @pytest.mark.parametrize("make", TINY)
-@pytest.mark.parametrize("mode", [dict(period=16), dict(period=0, tau=1e-3, restart=True)])
+@pytest.mark.parametrize("mode", [dict(period=16), dict(period=0, tau=1e-3, restart=True),
+                                  dict(period=16, deflate=True)])
 def test_mixed_reaches_fp64_accuracy(oracle_mod, make, mode):
     s = make()
     x_lu = oracle_mod.lu_solve(oracle_mod.dense(s), s.b)
@@ -173,6 +174,19 @@ def test_mixed_keeps_fp64_iteration_count(oracle_mod):
     assert rel.relres <= 1e-8 and rst.relres <= 1e-8
     assert rel.iters <= 1.1 * ref.iters + 2
     assert rst.iters > rel.iters
+
+
+def test_deflation_removes_the_pressure_mode(oracle_mod):
+    """On the pure-Neumann pressure case (one pinned cell) the constant vector
+    is a near-null mode; deflating it must cut the iteration count and still
+    give the FP64 solution."""
+    s = lc.config3(s=16)
+    plain = oracle_mod.mixed_pipecg(s, tol=1e-10, period=16)
+    defl = oracle_mod.mixed_pipecg(s, tol=1e-10, period=16, deflate=True)
+    assert plain.status == 0 and defl.status == 0 and defl.relres <= 1e-10
+    assert defl.iters <= 0.7 * plain.iters
+    xs = oracle_mod.pcg(s, tol=1e-13).x
+    assert np.linalg.norm(defl.x - xs) <= 1e-6 * np.linalg.norm(xs)
 
 
 # ---- pipelined == PCG, relabelling, edge cases -----------------------------------
