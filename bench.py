@@ -223,6 +223,11 @@ def run_ours(args):
                                          rr_period=args.rr_period)
         return st, it, rr, A.stats()["replacements"]
 
+    def mixed_deflated():
+        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="mixed",
+                                         rr_period=args.rr_period, deflate=True)
+        return st, it, rr, A.stats()["replacements"]
+
     def pcg64():
         _, st, it, rr = pkg.pcg_solve(A, b, x, tol=TOL)
         return st, it, rr, A.stats()["replacements"]
@@ -252,13 +257,17 @@ def run_ours(args):
 
     extra = {}
     if not args.skip_fp64:
+        t_defl, o_defl = timed(mixed_deflated, max(2, args.steps // 2), 1)
         t_pcg, o_pcg = timed(pcg64, max(2, args.steps // 2), 1)
         t_pipe, o_pipe = timed(pipe64, max(2, args.steps // 2), 1)
         pst, pit, prr, preps = o_pcg[-1]
         qst, qit, qrr, qreps = o_pipe[-1]
         mp = statistics.median(t_pcg)
         mq = statistics.median(t_pipe)
+        dst, dit, drr, dreps = o_defl[-1]
         extra = {
+            "mixed_deflated": {"s": statistics.median(t_defl), "iters": dit, "relres": drr,
+                               "status": dst, "replacements": dreps},
             "fp64_pcg": {"s": mp, "iters": pit, "relres": prr, "status": pst,
                          "alg_gbs": bytes_pcg64(n, F, pit, preps) / mp / 1e9},
             "fp64_pipecg": {"s": mq, "iters": qit, "relres": qrr, "status": qst,

@@ -67,6 +67,7 @@ struct SellView {
     const double *sd;       // [n_pad]
     const double *isd;      // [n_pad]
     const double *dg;       // [n_pad]
+    int meta_smem;          // 1: each block keeps its slices' (offset, width) in shared memory
 };
 
 // Barrier state shared by the blocks of one persistent launch.
@@ -113,8 +114,10 @@ namespace ldu {
 
 ldu::SellView view_of(const ldu_matrix *A);
 int cuda_status(cudaError_t e);
-int launch_persistent(const void *kernel, int grid, int block, void **args, cudaStream_t s);
-int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid);
+int launch_persistent(const void *kernel, int grid, int block, void **args, size_t smem,
+                      cudaStream_t s);
+int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid, size_t *smem);
+int meta_smem_bytes(int64_t n_slices, int num_sms, size_t *bytes);
 
 // ---------------------------------------------------------------------------
 // device helpers
@@ -466,14 +469,15 @@ template <>
 __device__ __forceinline__ const float *vals_of<float>(const SellView &A) { return A.val32; }
 
 // acc[j] += sum_k Ahat[row0 + j, col] * x[col] over the off-diagonal slots
-// of this lane's R rows in slice s.  Slots are taken KB at a time: all
-// column and value loads of a batch are issued before its gathers.
+// of this lane's R rows in the slice described by m = (first slot, width).
+// Slots are taken KB at a time: all column and value loads of a batch are
+// issued before its gathers.
 template <typename T, int R, int KB>
-__device__ __forceinline__ void sell_accum(const SellView &A, int s, int lane,
+__device__ __forceinline__ void sell_accum(const SellView &A, int2 m, int lane,
                                            const T *__restrict__ x, T (&acc)[R]) {
-    const int w = A.slice_w[s];
+    const int w = m.y;
     const int C = A.C;
-    const int base = A.slice_ptr[s] + R * lane;
+    const int base = m.x + R * lane;
     const T *__restrict__ val = vals_of<T>(A);
     for (int k0 = 0; k0 < w; k0 += KB) {
         int c[KB][R];
@@ -503,12 +507,12 @@ __device__ __forceinline__ void sell_accum(const SellView &A, int s, int lane,
 // Same, for two vectors gathered through the same slots (y1 = Ahat x1,
 // y2 = Ahat x2 share one read of the matrix).
 template <typename T, int R, int KB>
-__device__ __forceinline__ void sell_accum2(const SellView &A, int s, int lane,
+__device__ __forceinline__ void sell_accum2(const SellView &A, int2 m, int lane,
                                             const T *__restrict__ x1, const T *__restrict__ x2,
                                             T (&acc1)[R], T (&acc2)[R]) {
-    const int w = A.slice_w[s];
+    const int w = m.y;
     const int C = A.C;
-    const int base = A.slice_ptr[s] + R * lane;
+    const int base = m.x + R * lane;
     const T *__restrict__ val = vals_of<T>(A);
     for (int k0 = 0; k0 < w; k0 += KB) {
         int c[KB][R];
@@ -542,6 +546,25 @@ __device__ __forceinline__ SliceRange block_slices(int n_slices) {
     r.begin = (int)((b * n_slices) / G);
     r.end = (int)(((b + 1) * n_slices) / G);
     return r;
+}
+
+// Dynamic shared memory of the persistent kernels: (first slot, width) of
+// each slice the block owns, loaded once per launch, so the sweeps do not
+// wait on a global load before every slice's matrix loads.
+extern __shared__ int2 ldu_slice_meta[];
+
+__device__ __forceinline__ void load_slice_meta(const SellView &A, const SliceRange &range) {
+    if (A.meta_smem) {
+        for (int s = range.begin + (int)threadIdx.x; s < range.end; s += blockDim.x)
+            ldu_slice_meta[s - range.begin] = make_int2(A.slice_ptr[s], A.slice_w[s]);
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int2 slice_meta(const SellView &A, int s, const SliceRange &range) {
+    if (A.meta_smem)
+        return ldu_slice_meta[s - range.begin];
+    return make_int2(A.slice_ptr[s], A.slice_w[s]);
 }
 
 }  // namespace ldu

@@ -201,8 +201,10 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     CK(cudaGetLastError());
 
     const void *kern = (const void *)k_pcg64<4, Batch<4>::pcg>;   // pcg_solve's kernel for C = 128
+    size_t smem = 0;
+    meta_smem_bytes(n_slices, sms, &smem);
     int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNoallocBlock, 0));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNoallocBlock, smem));
     if (per_sm < 1)
         return LDU_ERR_UNSUPPORTED;
     const int grid = (int)std::min<int64_t>({(int64_t)per_sm * sms, (int64_t)sms * 32, kMaxGrid});
@@ -220,6 +222,7 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     P.A.sd = sd;
     P.A.isd = isd;
     P.A.dg = dg;
+    P.A.meta_smem = smem > 0;
     P.sync.count = bar_count;
     P.sync.err = bar_err;
     P.sync.timeout_ns = 10ull * 1000000000ull;
@@ -240,7 +243,7 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     P.deflate = 0;
     P.fault_inject = 0;
     void *args[] = {&P};
-    CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kNoallocBlock), args, 0, st));
+    CK(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kNoallocBlock), args, smem, st));
     SolveOut h{};
     int h_err = 0, h_flags = 0;
     CK(cudaMemcpyAsync(&h, out, sizeof(SolveOut), cudaMemcpyDeviceToHost, st));

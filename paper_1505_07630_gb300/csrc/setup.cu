@@ -40,12 +40,23 @@ SellView view_of(const ldu_matrix *A) {
     v.sd = A->sd;
     v.isd = A->isd;
     v.dg = A->dg;
+    v.meta_smem = 0;   // set by the launcher once the shared memory is sized
     return v;
 }
 
-int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid) {
+// Shared memory for the per-block slice metadata: enough for the largest
+// block share at one block per SM; 0 (global reads) above 48 KB.
+int meta_smem_bytes(int64_t n_slices, int num_sms, size_t *bytes) {
+    const int64_t per_block = (n_slices + num_sms - 1) / num_sms;
+    const int64_t b = per_block * (int64_t)sizeof(int2);
+    *bytes = b <= 48 * 1024 ? (size_t)b : 0;
+    return LDU_OK;
+}
+
+int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid, size_t *smem) {
+    meta_smem_bytes(A->n_slices, A->num_sms, smem);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, *smem);
     if (e != cudaSuccess)
         return cuda_status(e);
     if (per_sm < 1)
@@ -58,8 +69,9 @@ int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid) {
     return LDU_OK;
 }
 
-int launch_persistent(const void *kernel, int grid, int block, void **args, cudaStream_t s) {
-    cudaError_t e = cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(block), args, 0, s);
+int launch_persistent(const void *kernel, int grid, int block, void **args, size_t smem,
+                      cudaStream_t s) {
+    cudaError_t e = cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(block), args, smem, s);
     return cuda_status(e);
 }
 

@@ -95,11 +95,13 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     }
     const void *kern = pick_kernel(A, (kind == kMixed && opt.deflate) ? kMixedDeflated : kind);
     int grid = 0;
-    int rc = grid_for(A, kern, A->block_threads, &grid);
+    size_t smem = 0;
+    int rc = grid_for(A, kern, A->block_threads, &grid, &smem);
     if (rc != LDU_OK)
         return rc;
     SolveParams P;
     P.A = view_of(A);
+    P.A.meta_smem = smem > 0;
     P.sync.count = A->bar_count;
     P.sync.err = A->bar_err;
     const double tmo = opt.barrier_timeout_s > 0.0 ? opt.barrier_timeout_s : 10.0;
@@ -127,7 +129,7 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     if ((e = cudaMemsetAsync(A->out_dev, 0xff, sizeof(SolveOut), st)) != cudaSuccess)
         return cuda_status(e);
     void *args[] = {&P};
-    rc = launch_persistent(kern, grid, A->block_threads, args, st);
+    rc = launch_persistent(kern, grid, A->block_threads, args, smem, st);
     if (rc != LDU_OK)
         return rc;
     int flags_err[2] = {0, 0};

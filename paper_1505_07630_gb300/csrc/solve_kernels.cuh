@@ -173,7 +173,7 @@ __device__ __forceinline__ void residual64_pass(const SolveParams &P, const doub
         const int row0 = s * A.C + R * lane;
         double acc[R], bb[R], dd[R];
         ld_rows<R>(xh + row0, acc);
-        sell_accum<double, R, KB>(A, s, lane, xh, acc);
+        sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, xh, acc);
         ld_rows<R>(bh + row0, bb);
         ld_rows<R>(A.dg + row0, dd);
 #pragma unroll
@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
     if (P.fault_inject && blockIdx.x == 0)
         return;   // test hook: this block never arrives at a barrier
     LANE_ROWS;
+    load_slice_meta(P.A, range);
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *r = P.v64[2], *p = P.v64[3], *q = P.v64[4];
     __shared__ PcgCtl ctl;
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 pp[j] = acc[j];
-            sell_accum<double, R, KB>(A, s, lane, p, acc);
+            sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, p, acc);
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 pq = fma(pp[j], acc[j], pq);
@@ -384,7 +385,7 @@ __device__ __forceinline__ bool pipe64_replace(const SolveParams &P, double *w, 
         double aw[R], as[R];
         ld_rows<R>(r + row0, aw);
         ld_rows<R>(p + row0, as);
-        sell_accum2<double, R, KB>(A, s, lane, r, p, aw, as);
+        sell_accum2<double, R, KB>(A, slice_meta(A, s, range), lane, r, p, aw, as);
         st_rows<R>(w + row0, aw);
         st_rows<R>(sv + row0, as);
     }
@@ -396,7 +397,7 @@ __device__ __forceinline__ bool pipe64_replace(const SolveParams &P, double *w, 
         const int row0 = s * A.C + R * lane;
         double az[R], rr[R], ww[R], dd[R];
         ld_rows<R>(sv + row0, az);
-        sell_accum<double, R, KB>(A, s, lane, sv, az);
+        sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, sv, az);
         st_rows<R>(z + row0, az);
         ld_rows<R>(r + row0, rr);
         ld_rows<R>(w + row0, ww);
@@ -421,6 +422,7 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
     if (P.fault_inject && blockIdx.x == 0)
         return;
     LANE_ROWS;
+    load_slice_meta(P.A, range);
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *r = P.v64[2];
     double *wa = P.v64[3], *wb = P.v64[4];
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 nn[j] = ww[j];
-            sell_accum<double, R, KB>(A, s, lane, w, nn);
+            sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, w, nn);
             double zz[R], ss[R], pp[R], xx[R], rr[R], dd[R];
             ld_rows<R>(z + row0, zz);
             ld_rows<R>(sv + row0, ss);
@@ -606,6 +608,7 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
     if (P.fault_inject && blockIdx.x == 0)
         return;
     LANE_ROWS;
+    load_slice_meta(P.A, range);
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *rt = P.v64[2], *w0 = P.v64[3], *q0 = P.v64[4];
     float *xc = P.v32[0], *r = P.v32[1], *wa = P.v32[2], *wb = P.v32[3];
@@ -671,7 +674,7 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 ww[j] = acc[j];
-            sell_accum<double, R, KB>(A, s, lane, w0, acc);
+            sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, w0, acc);
 #pragma unroll
             for (int j = 0; j < R; ++j) {
                 pc[0] = fma(ww[j], acc[j], pc[0]);
@@ -688,7 +691,7 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             double acc[R];
             float tf[R];
             ld_rows<R>(q0 + row0, acc);
-            sell_accum<double, R, KB>(A, s, lane, q0, acc);
+            sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, q0, acc);
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 tf[j] = (float)acc[j];
@@ -746,7 +749,7 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                     const int row0 = s * A.C + R * lane;
                     double acc[R], bb[R], dd[R];
                     ld_rows<R>(xh + row0, acc);
-                    sell_accum<double, R, KB>(A, s, lane, xh, acc);
+                    sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, xh, acc);
                     ld_rows<R>(bh + row0, bb);
                     ld_rows<R>(A.dg + row0, dd);
                     float rf[R];
@@ -765,7 +768,7 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                     const int row0 = s * A.C + R * lane;
                     double acc[R], bb[R], ww[R];
                     ld_rows<R>(xh + row0, acc);
-                    sell_accum<double, R, KB>(A, s, lane, xh, acc);
+                    sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, xh, acc);
                     ld_rows<R>(bh + row0, bb);
                     ld_rows<R>(w0 + row0, ww);
 #pragma unroll
@@ -839,7 +842,7 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                 float aw[R], as[R];
                 ld_rows<R>(r + row0, aw);
                 ld_rows<R>(p + row0, as);
-                sell_accum2<float, R, KB>(A, s, lane, r, p, aw, as);
+                sell_accum2<float, R, KB>(A, slice_meta(A, s, range), lane, r, p, aw, as);
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
                     aw[j] *= f;
@@ -856,7 +859,7 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                 const int row0 = s * A.C + R * lane;
                 float az[R], rr[R], pp[R], ww[R], qq[R];
                 ld_rows<R>(sv + row0, az);
-                sell_accum<float, R, KB>(A, s, lane, sv, az);
+                sell_accum<float, R, KB>(A, slice_meta(A, s, range), lane, sv, az);
                 st_rows<R>(z + row0, az);
                 ld_rows<R>(r + row0, rr);
                 ld_rows<R>(p + row0, pp);
@@ -940,7 +943,7 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 nn[j] = ww[j];
-            sell_accum<float, R, KB>(A, s, lane, w, nn);
+            sell_accum<float, R, KB>(A, slice_meta(A, s, range), lane, w, nn);
             float zz[R], ss[R], pp[R], xx[R], rr[R];
             ld_rows<R>(z + row0, zz);
             ld_rows<R>(sv + row0, ss);
