@@ -206,6 +206,57 @@ void ldu_destroy(ldu_matrix *A);
 /* A static string naming a status code. */
 const char *ldu_status_string(int status);
 
+/* ---- batches of independent systems -------------------------------------
+ * Many systems of uneven size (the laplacianFoam / icoFoam solve repeated
+ * over independent meshes) solved by one persistent cooperative launch:
+ * each system is solved by a team of blocks sized to its work (one block
+ * for small systems), with per-system scalars, stopping tests and status. */
+
+/* Team sizing of a batched launch.  A zeroed struct selects the defaults. */
+typedef struct batch_opts {
+    int max_team;            /* largest team of blocks on one system (default 32) */
+    double team_work_scale;  /* multiplies the work per block that sizes teams;
+                                above 1 gives smaller teams (default 1) */
+} batch_opts;
+
+/* Create a batched handle.
+ *   nsys            number of systems (> 0)
+ *   n, nFaces       host int64[nsys]: cells and internal faces of each system
+ *   owner, neighbour, diag, upper, lower
+ *                   device arrays of all systems concatenated in order; face
+ *                   indices are local to their system (0-based, owner < neighbour)
+ * Other arguments and errors as ldu_create; a face outside its own system is
+ * BAD_ADDRESSING.  Synchronises stream. */
+int ldu_create_batched(int nsys, const int64_t *n, const int64_t *nFaces, const int32_t *owner,
+                       const int32_t *neighbour, const double *diag, const double *upper,
+                       const double *lower, const ldu_opts *opt, ldu_stream_t stream,
+                       ldu_matrix **out);
+
+/* Recompute the team schedule of a batched handle (synchronises stream). */
+int ldu_batch_schedule(ldu_matrix *A, const batch_opts *opts, ldu_stream_t stream);
+
+/* Facts about a batched handle (host outputs, each may be NULL). */
+int ldu_batch_info(const ldu_matrix *A, int *nsys, int *grid_blocks, int *ntasks, int *max_team);
+
+/* Queue the solve of every system of a batched handle (precision LDU_FP64:
+ * Jacobi-PCG; LDU_MIXED: the mixed pipelined method of pipecg_solve), with
+ * the caller's concatenated device b and x (x: initial guesses in,
+ * solutions out).  Does not synchronise and allocates nothing, so it can be
+ * captured in a CUDA graph; ldu_batch_results reads the outcome. */
+int pcg_solve_batched_async(const ldu_matrix *A, const double *b, double *x, double tol,
+                            int maxit, int precision, const pcg_opts *opts, ldu_stream_t stream);
+
+/* Per-system outcome of the last batched solve (host arrays of nsys entries,
+ * each may be NULL): iterations, true relative residual, status.  Returns
+ * the worst status.  Synchronises stream. */
+int ldu_batch_results(const ldu_matrix *A, int *iters, double *relres, int *status,
+                      ldu_stream_t stream);
+
+/* pcg_solve_batched_async followed by ldu_batch_results. */
+int pcg_solve_batched(const ldu_matrix *A, const double *b, double *x, double tol, int maxit,
+                      int precision, const pcg_opts *opts, int *iters, double *relres,
+                      int *status, ldu_stream_t stream);
+
 /* Jacobi-PCG on a small LDU system without any device allocation.  The paper
  * has no counterpart: this exists for callers that cannot call cudaMalloc
  * (their device memory is owned by another allocator, such as a framework's

@@ -4,7 +4,9 @@ The compute path is libldupcg (hand-written sm_103a CUDA behind a C ABI,
 include/ldupcg.h); this package holds its build script, the ctypes binding
 and the autograd wrapper.  PyTorch supplies device memory and streams only.
 """
-from .ldupcg import (LduError, LduMatrix, from_system, ldu_create, ldu_destroy,  # noqa: F401
+from .ldupcg import (LduError, LduMatrix, from_system, from_systems, ldu_batch_info,  # noqa: F401
+                     ldu_batch_results, ldu_batch_schedule, ldu_create, ldu_create_batched,
+                     ldu_destroy, pcg_solve_batched, pcg_solve_batched_async,
                      ldu_face_grad, ldu_set_face_coeffs, ldu_spmv, ldu_update_values, lib,
                      library_path, pcg_solve, pcg_solve_ldu_noalloc, pipecg_solve,
                      status_string)

@@ -26,6 +26,7 @@ constexpr int kNumDots = 4;            // doubles per block in a reduction slot
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr uint32_t kLowerBit = 0x80000000u;
 constexpr uint32_t kPadFid = 0xffffffffu;
+constexpr int kMetaSmemMax = 32 * 1024;   // dynamic shared memory for slice metadata
 
 // error bits raised by device-side validation
 enum : int {
@@ -108,6 +109,7 @@ struct ldu_matrix {
     ldu::SolveOut *out_host;   // pinned host
     int *flags_dev;            // validation flags
     ldu_solve_stats last;
+    struct ldu_batch *batch;   // systems of a batched handle (NULL otherwise)
 };
 
 namespace ldu {
@@ -134,29 +136,38 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     return v;
 }
 
-// Grid-wide barrier for a cooperative launch.  `epoch` counts the barriers
+// Barrier over `members` blocks of a cooperative launch (all of them, or a
+// team that solves one system of a batch).  `epoch` counts the barriers
 // this block has passed; arrivals accumulate in one counter that is never
 // reset during the launch.  Arrival is a release-add by thread 0 after the
 // block's __syncthreads (cumulative over the block's writes); the wait is an
 // acquire-load spin, so the block's later reads see every write made before
 // any block's arrival.  Every spin is bounded: after timeout_ns the block
-// records kDevTimeout and leaves; the others then time out at the next
-// barrier, which that block never reaches.  Returns false when the launch
+// records kDevTimeout and leaves, and every other spinning block sees the
+// record within a few polls and leaves too.  Returns false when the launch
 // must stop.
 __device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool grid_sync(const GridSync &g, unsigned &epoch) {
+__device__ __forceinline__ bool team_sync(const GridSync &g, unsigned &epoch, unsigned members) {
     __shared__ int s_fail;
     __syncthreads();
     epoch += 1;
     if (threadIdx.x == 0) {
-        const unsigned target = epoch * gridDim.x;
+        const unsigned target = epoch * members;
         red_release_add_u32(g.count, 1u);
         int fail = 0;
+        unsigned polls = 0;
         const unsigned long long t0 = global_ns();
         while ((int)(ld_acquire_u32(g.count) - target) < 0) {
+            // every 16 polls: leave at once if any block has already failed
+            // (so a failure in one team of a batch does not leave the others
+            // waiting out their own time limits one after another)
+            if ((++polls & 15u) == 0 && *(volatile int *)g.err != 0) {
+                fail = 1;
+                break;
+            }
             if (global_ns() - t0 > g.timeout_ns) {
                 atomicCAS(g.err, 0, kDevTimeout);
                 fail = 1;
@@ -208,7 +219,7 @@ __device__ __forceinline__ void block_sum_to_slot(double (&v)[K], double *slot) 
 // all blocks hold bitwise-identical totals.  All slot loads of a thread are
 // independent, so the sum costs about one L2 round trip.
 template <int K>
-__device__ __forceinline__ void grid_total(const double *slots, double (&out)[K]) {
+__device__ __forceinline__ void grid_total(const double *slots, double (&out)[K], int members) {
     __shared__ double sm[32][K];
     __shared__ double res[K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -217,7 +228,7 @@ __device__ __forceinline__ void grid_total(const double *slots, double (&out)[K]
 #pragma unroll
     for (int k = 0; k < K; ++k)
         t[k] = 0.0;
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x)
+    for (int c = threadIdx.x; c < members; c += blockDim.x)
 #pragma unroll
         for (int k = 0; k < K; ++k)
             t[k] += __ldcg(slots + (size_t)c * kNumDots + k);
@@ -327,7 +338,7 @@ __device__ __forceinline__ void block_sum_ff(FF (&v)[K], float2 *slot) {
 
 // Float-pair grid total after a barrier (same fixed order in every block).
 template <int K>
-__device__ __forceinline__ void grid_total_ff(const float2 *slots, double (&out)[K]) {
+__device__ __forceinline__ void grid_total_ff(const float2 *slots, double (&out)[K], int members) {
     __shared__ FF sm[32][K];
     __shared__ double res[K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -336,7 +347,7 @@ __device__ __forceinline__ void grid_total_ff(const float2 *slots, double (&out)
 #pragma unroll
     for (int k = 0; k < K; ++k)
         t[k] = FF{0.0f, 0.0f};
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += blockDim.x)
+    for (int c = threadIdx.x; c < members; c += blockDim.x)
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const float2 v = __ldcg(slots + (size_t)c * kNumDots + k);

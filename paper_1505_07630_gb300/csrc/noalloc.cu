@@ -227,6 +227,7 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     P.sync.err = bar_err;
     P.sync.timeout_ns = 10ull * 1000000000ull;
     P.slots = slots;
+    P.tasks = nullptr;
     P.out = out;
     P.b = b;
     P.x = x;

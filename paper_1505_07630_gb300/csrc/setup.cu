@@ -45,11 +45,13 @@ SellView view_of(const ldu_matrix *A) {
 }
 
 // Shared memory for the per-block slice metadata: enough for the largest
-// block share at one block per SM; 0 (global reads) above 48 KB.
+// block share at one block per SM; 0 (global reads) above kMetaSmemMax, so
+// that with the kernels' static shared memory a block stays within the
+// default 48 KB.
 int meta_smem_bytes(int64_t n_slices, int num_sms, size_t *bytes) {
     const int64_t per_block = (n_slices + num_sms - 1) / num_sms;
     const int64_t b = per_block * (int64_t)sizeof(int2);
-    *bytes = b <= 48 * 1024 ? (size_t)b : 0;
+    *bytes = b <= kMetaSmemMax ? (size_t)b : 0;
     return LDU_OK;
 }
 
@@ -96,9 +98,18 @@ cudaError_t dev_alloc(T **p, int64_t count, int64_t *bytes) {
     return e;
 }
 
+}  // namespace
+
+namespace ldu {
+void free_batch(ldu_matrix *A);   // solve_batched.cu
+}
+
+namespace {
+
 void free_handle(ldu_matrix *A) {
     if (!A)
         return;
+    ldu::free_batch(A);
     void *ptrs[] = {A->slice_ptr, A->slice_w, A->col, A->fid, A->owner, A->neighbour,
                     A->val64, A->sd, A->isd, A->dg, A->val32, A->slots, A->bar_count,
                     A->bar_err, A->out_dev, A->flags_dev};

@@ -107,6 +107,7 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     const double tmo = opt.barrier_timeout_s > 0.0 ? opt.barrier_timeout_s : 10.0;
     P.sync.timeout_ns = (unsigned long long)(tmo * 1e9);
     P.slots = A->slots;
+    P.tasks = nullptr;
     P.out = A->out_dev;
     P.b = b;
     P.x = x;

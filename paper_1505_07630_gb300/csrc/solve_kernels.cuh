@@ -25,7 +25,8 @@ using namespace ldu;
 struct SolveParams {
     SellView A;
     GridSync sync;
-    double *slots;       // [2][gridDim.x][kNumDots]; FF sums use the same cells as float2
+    double *slots;       // reduction slots of the scopes; FF sums use the cells as float2
+    const int *tasks;    // batched launches: per-block task lists (see solve_batched.cu)
     SolveOut *out;
     const double *b;     // caller, n entries
     double *x;           // caller, n entries: x0 in, solution out
@@ -40,11 +41,52 @@ struct SolveParams {
     int fault_inject;
 };
 
-__device__ __forceinline__ double *slot_of(const SolveParams &P, int parity) {
-    return P.slots + ((size_t)parity * gridDim.x + blockIdx.x) * kNumDots;
+// The blocks that solve one system together and what they share: the whole
+// grid for a single solve, a team of blocks (or one block) for one system of
+// a batch.  Barriers and reductions are scoped to these members.
+struct Scope {
+    int members;          // blocks in the scope
+    int rank;             // this block's rank in it
+    unsigned *count;      // barrier counter of the scope (unused when members == 1)
+    double *slots;        // [2][members][kNumDots] reduction slots
+    SliceRange range;     // slices this block sweeps
+    int row0;             // first row of the system in the padded layout
+    int n;                // real rows of the system
+    long long b_off;      // offset of the system in the caller's b and x
+    int id;               // index of the system's SolveOut
+};
+
+__device__ __forceinline__ double *slot_of(const Scope &sc, int parity) {
+    return sc.slots + ((size_t)parity * sc.members + sc.rank) * kNumDots;
 }
-__device__ __forceinline__ const double *slots_all(const SolveParams &P, int parity) {
-    return P.slots + (size_t)parity * gridDim.x * kNumDots;
+__device__ __forceinline__ const double *slots_all(const Scope &sc, int parity) {
+    return sc.slots + (size_t)parity * sc.members * kNumDots;
+}
+
+// Barrier over the scope's blocks; a one-block scope needs only __syncthreads.
+__device__ __forceinline__ bool scope_sync(const Scope &sc, const GridSync &g, unsigned &epoch) {
+    if (sc.members == 1) {
+        __syncthreads();
+        return true;
+    }
+    GridSync t = g;
+    t.count = sc.count;
+    return team_sync(t, epoch, (unsigned)sc.members);
+}
+
+// The whole grid as one scope (single-system launch).
+__device__ __forceinline__ Scope grid_scope(const SolveParams &P) {
+    Scope sc;
+    sc.members = gridDim.x;
+    sc.rank = blockIdx.x;
+    sc.count = P.sync.count;
+    sc.slots = P.slots;
+    sc.range = block_slices(P.A.n_slices);
+    sc.row0 = 0;
+    sc.n = P.A.n;
+    sc.b_off = 0;
+    sc.id = 0;
+    return sc;
 }
 
 // Slots taken per batch by sell_accum for each solver and rows per lane R:
@@ -60,24 +102,24 @@ struct Batch {
 // FP64 reduction of K partials: block sums -> slot -> barrier -> totals.
 // Returns false when the barrier failed (the kernel must return).
 template <int K>
-__device__ __forceinline__ bool reduce_d(const SolveParams &P, double (&part)[K], double (&tot)[K],
-                                         unsigned &epoch, int &parity) {
-    block_sum_to_slot<K>(part, slot_of(P, parity));
-    if (!grid_sync(P.sync, epoch))
+__device__ __forceinline__ bool reduce_d(const SolveParams &P, const Scope &sc, double (&part)[K],
+                                         double (&tot)[K], unsigned &epoch, int &parity) {
+    block_sum_to_slot<K>(part, slot_of(sc, parity));
+    if (!scope_sync(sc, P.sync, epoch))
         return false;
-    grid_total<K>(slots_all(P, parity), tot);
+    grid_total<K>(slots_all(sc, parity), tot, sc.members);
     parity ^= 1;
     return true;
 }
 
 // The same with float-pair arithmetic (per-iteration dot products).
 template <int K>
-__device__ __forceinline__ bool reduce_f(const SolveParams &P, FF (&part)[K], double (&tot)[K],
-                                         unsigned &epoch, int &parity) {
-    block_sum_ff<K>(part, reinterpret_cast<float2 *>(slot_of(P, parity)));
-    if (!grid_sync(P.sync, epoch))
+__device__ __forceinline__ bool reduce_f(const SolveParams &P, const Scope &sc, FF (&part)[K],
+                                         double (&tot)[K], unsigned &epoch, int &parity) {
+    block_sum_ff<K>(part, reinterpret_cast<float2 *>(slot_of(sc, parity)));
+    if (!scope_sync(sc, P.sync, epoch))
         return false;
-    grid_total_ff<K>(reinterpret_cast<const float2 *>(slots_all(P, parity)), tot);
+    grid_total_ff<K>(reinterpret_cast<const float2 *>(slots_all(sc, parity)), tot, sc.members);
     parity ^= 1;
     return true;
 }
@@ -94,7 +136,7 @@ __device__ __forceinline__ double inv_pow2(double x) {
     const int lane = threadIdx.x & 31;                        \
     const int warp = threadIdx.x >> 5;                        \
     const int nwarps = blockDim.x >> 5;                       \
-    const SliceRange range = block_slices(P.A.n_slices);      \
+    const SliceRange range = sc.range;                        \
     (void)range
 
 #define FOR_MY_SLICES(s) for (int s = range.begin + warp; s < range.end; s += nwarps)
@@ -102,16 +144,20 @@ __device__ __forceinline__ double inv_pow2(double x) {
 // pass 0 of every solver: bhat = b / sd, xhat = x0 * sd (rows < n); partial
 // ||b||^2 in part[0]
 template <int R>
-__device__ __forceinline__ void prep_pass(const SolveParams &P, double *bh, double *xh, double (&part)[1]) {
+__device__ __forceinline__ void prep_pass(const SolveParams &P, const Scope &sc, double *bh,
+                                          double *xh, double (&part)[1]) {
     LANE_ROWS;
     const SellView &A = P.A;
+    const double *b = P.b + sc.b_off;
+    const double *x = P.x + sc.b_off;
     FOR_MY_SLICES(s) {
         const int row0 = s * A.C + R * lane;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const int r = row0 + j;
-            const double bi = r < A.n ? P.b[r] : 0.0;
-            const double xi = r < A.n ? P.x[r] : 0.0;
+            const int i = r - sc.row0;
+            const double bi = i < sc.n ? b[i] : 0.0;
+            const double xi = i < sc.n ? x[i] : 0.0;
             bh[r] = bi * A.isd[r];
             xh[r] = xi * A.sd[r];
             part[0] = fma(bi, bi, part[0]);
@@ -120,7 +166,7 @@ __device__ __forceinline__ void prep_pass(const SolveParams &P, double *bh, doub
 }
 
 template <typename T, int R>
-__device__ __forceinline__ void zero_rows(const SolveParams &P, T *v) {
+__device__ __forceinline__ void zero_rows(const SolveParams &P, const Scope &sc, T *v) {
     LANE_ROWS;
     FOR_MY_SLICES(s) {
         T z[R];
@@ -133,40 +179,46 @@ __device__ __forceinline__ void zero_rows(const SolveParams &P, T *v) {
 
 // x = xhat / sd for rows < n
 template <int R>
-__device__ __forceinline__ void unscale_pass(const SolveParams &P, const double *xh) {
+__device__ __forceinline__ void unscale_pass(const SolveParams &P, const Scope &sc,
+                                             const double *xh) {
     LANE_ROWS;
     const SellView &A = P.A;
+    double *x = P.x + sc.b_off;
     FOR_MY_SLICES(s) {
         const int row0 = s * A.C + R * lane;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const int r = row0 + j;
-            if (r < A.n)
-                P.x[r] = xh[r] * A.isd[r];
+            const int i = r - sc.row0;
+            if (i < sc.n)
+                x[i] = xh[r] * A.isd[r];
         }
     }
 }
 
-__device__ __forceinline__ void zero_solution(const SolveParams &P) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.A.n; r += gridDim.x * blockDim.x)
-        P.x[r] = 0.0;
+__device__ __forceinline__ void zero_solution(const SolveParams &P, const Scope &sc) {
+    double *x = P.x + sc.b_off;
+    for (int i = sc.rank * blockDim.x + threadIdx.x; i < sc.n; i += sc.members * blockDim.x)
+        x[i] = 0.0;
 }
 
-__device__ __forceinline__ void write_out(const SolveParams &P, int status, int iters, int reps,
-                                          double relres, double bnorm) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        P.out->status = status;
-        P.out->iters = iters;
-        P.out->replacements = reps;
-        P.out->relres = relres;
-        P.out->bnorm = bnorm;
+__device__ __forceinline__ void write_out(const SolveParams &P, const Scope &sc, int status,
+                                          int iters, int reps, double relres, double bnorm) {
+    if (sc.rank == 0 && threadIdx.x == 0) {
+        SolveOut *o = P.out + sc.id;
+        o->status = status;
+        o->iters = iters;
+        o->replacements = reps;
+        o->relres = relres;
+        o->bnorm = bnorm;
     }
 }
 
 // r = bhat - (I + Ahat_off) xhat (FP64); partials (r,r) and sum d r^2
 template <int R, int KB>
-__device__ __forceinline__ void residual64_pass(const SolveParams &P, const double *bh,
-                                                const double *xh, double *r, double (&part)[2]) {
+__device__ __forceinline__ void residual64_pass(const SolveParams &P, const Scope &sc,
+                                                const double *bh, const double *xh, double *r,
+                                                double (&part)[2]) {
     LANE_ROWS;
     const SellView &A = P.A;
     FOR_MY_SLICES(s) {
@@ -195,11 +247,10 @@ struct PcgCtl {
 };
 
 template <int R, int KB>
-__global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
-    if (P.fault_inject && blockIdx.x == 0)
-        return;   // test hook: this block never arrives at a barrier
+__device__ __forceinline__ bool pcg64_body(const SolveParams &P, const Scope &sc) {
+    __syncthreads();   // the previous body of this block is done with shared state
     LANE_ROWS;
-    load_slice_meta(P.A, range);
+    load_slice_meta(P.A, sc.range);
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *r = P.v64[2], *p = P.v64[3], *q = P.v64[4];
     __shared__ PcgCtl ctl;
@@ -208,21 +259,21 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
     int parity = 0;
 
     double b2[1] = {0.0}, t1[1];
-    prep_pass<R>(P, bh, xh, b2);
-    zero_rows<double, R>(P, p);   // the first p = r + 0 * p must not see stale values
-    if (!reduce_d<1>(P, b2, t1, epoch, parity))
-        return;
+    prep_pass<R>(P, sc, bh, xh, b2);
+    zero_rows<double, R>(P, sc, p);   // the first p = r + 0 * p must not see stale values
+    if (!reduce_d<1>(P, sc, b2, t1, epoch, parity))
+        return false;
     const double bn2 = t1[0];
     if (bn2 == 0.0) {
-        zero_solution(P);
-        write_out(P, kDevOk, 0, 0, 0.0, 0.0);
-        return;
+        zero_solution(P, sc);
+        write_out(P, sc, kDevOk, 0, 0, 0.0, 0.0);
+        return true;
     }
     const double thr2 = P.tol * P.tol * bn2;   // stop when sum d r^2 <= tol^2 ||b||^2
     double part[2] = {0.0, 0.0}, tot[2];
-    residual64_pass<R, KB>(P, bh, xh, r, part);
-    if (!reduce_d<2>(P, part, tot, epoch, parity))
-        return;
+    residual64_pass<R, KB>(P, sc, bh, xh, r, part);
+    if (!reduce_d<2>(P, sc, part, tot, epoch, parity))
+        return false;
     // thread-0 state
     double gamma = tot[0], rho = tot[1];
     int status = kDevNotConverged, it = 0, reps = 1;
@@ -249,8 +300,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
                 pp[j] = fma(beta, pp[j], rr[j]);
             st_rows<R>(p + row0, pp);
         }
-        if (!grid_sync(P.sync, epoch))
-            return;
+        if (!scope_sync(sc, P.sync, epoch))
+            return false;
         if (t0 && it >= P.maxit) {
             ctl.exit = 1;
             status = kDevNotConverged;
@@ -275,8 +326,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
         }
         FF fpq[1] = {ff_from_double(pq * sg)};
         double tpq[1];
-        if (!reduce_f<1>(P, fpq, tpq, epoch, parity))
-            return;
+        if (!reduce_f<1>(P, sc, fpq, tpq, epoch, parity))
+            return false;
         if (t0) {
             const double pqv = tpq[0] / sg;
             if (!(pqv > 0.0)) {
@@ -312,8 +363,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
         }
         FF fr[2] = {ff_from_double(g0 * sg), ff_from_double(g1 * sr)};
         double tr[2];
-        if (!reduce_f<2>(P, fr, tr, epoch, parity))
-            return;
+        if (!reduce_f<2>(P, sc, fr, tr, epoch, parity))
+            return false;
         if (t0) {
             ++it;
             ctl.truth = 0;
@@ -331,9 +382,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
         if (ctl.check) {
             // confirm with the true residual; restart the search if it disagrees
             double pt[2] = {0.0, 0.0}, tt[2];
-            residual64_pass<R, KB>(P, bh, xh, r, pt);
-            if (!reduce_d<2>(P, pt, tt, epoch, parity))
-                return;
+            residual64_pass<R, KB>(P, sc, bh, xh, r, pt);
+            if (!reduce_d<2>(P, sc, pt, tt, epoch, parity))
+                return false;
             if (t0) {
                 ++reps;
                 ctl.truth = 1;
@@ -351,33 +402,42 @@ __global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
     }
     if (!ctl.truth) {
         double pt[2] = {0.0, 0.0}, tt[2];
-        residual64_pass<R, KB>(P, bh, xh, r, pt);
-        if (!reduce_d<2>(P, pt, tt, epoch, parity))
-            return;
+        residual64_pass<R, KB>(P, sc, bh, xh, r, pt);
+        if (!reduce_d<2>(P, sc, pt, tt, epoch, parity))
+            return false;
         if (t0) {
             ++reps;
             rho = tt[1];
         }
     }
-    unscale_pass<R>(P, xh);
+    unscale_pass<R>(P, sc, xh);
     if (t0)
-        write_out(P, status, it, reps, sqrt(rho / bn2), sqrt(bn2));
+        write_out(P, sc, status, it, reps, sqrt(rho / bn2), sqrt(bn2));
+    return true;
+}
+
+template <int R, int KB>
+__global__ void __launch_bounds__(256, 2) k_pcg64(SolveParams P) {
+    if (P.fault_inject && blockIdx.x == 0)
+        return;   // test hook: this block never arrives at a barrier
+    const Scope sc = grid_scope(P);
+    pcg64_body<R, KB>(P, sc);
 }
 
 // ============================================================================
 // pipelined PCG, FP64
 // v64: 0 xhat, 1 bhat, 2 r, 3 w(a), 4 w(b), 5 z, 6 s, 7 p
 template <int R, int KB>
-__device__ __forceinline__ bool pipe64_replace(const SolveParams &P, double *w, double (&tot)[3],
-                                               unsigned &epoch, int &parity) {
+__device__ __forceinline__ bool pipe64_replace(const SolveParams &P, const Scope &sc, double *w,
+                                               double (&tot)[3], unsigned &epoch, int &parity) {
     LANE_ROWS;
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *r = P.v64[2];
     double *z = P.v64[5], *sv = P.v64[6], *p = P.v64[7];
     // r = bhat - Ahat xhat
     double d2[2] = {0.0, 0.0};
-    residual64_pass<R, KB>(P, bh, xh, r, d2);
-    if (!grid_sync(P.sync, epoch))
+    residual64_pass<R, KB>(P, sc, bh, xh, r, d2);
+    if (!scope_sync(sc, P.sync, epoch))
         return false;
     // w = Ahat r ; s = Ahat p
     FOR_MY_SLICES(s) {
@@ -389,7 +449,7 @@ __device__ __forceinline__ bool pipe64_replace(const SolveParams &P, double *w, 
         st_rows<R>(w + row0, aw);
         st_rows<R>(sv + row0, as);
     }
-    if (!grid_sync(P.sync, epoch))
+    if (!scope_sync(sc, P.sync, epoch))
         return false;
     // z = Ahat s ; gamma = (r,r), delta = (w,r), rho = sum d r^2
     double part[3] = {0.0, 0.0, 0.0};
@@ -409,7 +469,7 @@ __device__ __forceinline__ bool pipe64_replace(const SolveParams &P, double *w, 
             part[2] = fma(dd[j] * rr[j], rr[j], part[2]);
         }
     }
-    return reduce_d<3>(P, part, tot, epoch, parity);
+    return reduce_d<3>(P, sc, part, tot, epoch, parity);
 }
 
 struct PipeCtl {
@@ -418,11 +478,10 @@ struct PipeCtl {
 };
 
 template <int R, int KB>
-__global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
-    if (P.fault_inject && blockIdx.x == 0)
-        return;
+__device__ __forceinline__ bool pipe64_body(const SolveParams &P, const Scope &sc) {
+    __syncthreads();   // the previous body of this block is done with shared state
     LANE_ROWS;
-    load_slice_meta(P.A, range);
+    load_slice_meta(P.A, sc.range);
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *r = P.v64[2];
     double *wa = P.v64[3], *wb = P.v64[4];
@@ -433,22 +492,22 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
     int parity = 0, wc = 0;
 
     double b2[1] = {0.0}, t1[1];
-    prep_pass<R>(P, bh, xh, b2);
-    zero_rows<double, R>(P, p);
-    zero_rows<double, R>(P, z);
-    zero_rows<double, R>(P, sv);
-    if (!reduce_d<1>(P, b2, t1, epoch, parity))
-        return;
+    prep_pass<R>(P, sc, bh, xh, b2);
+    zero_rows<double, R>(P, sc, p);
+    zero_rows<double, R>(P, sc, z);
+    zero_rows<double, R>(P, sc, sv);
+    if (!reduce_d<1>(P, sc, b2, t1, epoch, parity))
+        return false;
     const double bn2 = t1[0];
     if (bn2 == 0.0) {
-        zero_solution(P);
-        write_out(P, kDevOk, 0, 0, 0.0, 0.0);
-        return;
+        zero_solution(P, sc);
+        write_out(P, sc, kDevOk, 0, 0, 0.0, 0.0);
+        return true;
     }
     const double thr2 = P.tol * P.tol * bn2;
     double tot[3];
-    if (!pipe64_replace<R, KB>(P, wa, tot, epoch, parity))
-        return;
+    if (!pipe64_replace<R, KB>(P, sc, wa, tot, epoch, parity))
+        return false;
     // thread-0 state
     int reps = 1, it = 0, since = 0, status = kDevNotConverged;
     bool truth = true, fresh = true;
@@ -498,8 +557,8 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
             break;
         double *w = wc ? wb : wa;
         if (action == 1) {
-            if (!pipe64_replace<R, KB>(P, w, tot, epoch, parity))
-                return;
+            if (!pipe64_replace<R, KB>(P, sc, w, tot, epoch, parity))
+                return false;
             if (t0) {
                 ++reps;
                 since = 0;
@@ -549,8 +608,8 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
         }
         FF fp[3] = {ff_from_double(g0 * sg), ff_from_double(g1 * sg), ff_from_double(g2 * sr)};
         double tp[3];
-        if (!reduce_f<3>(P, fp, tp, epoch, parity))
-            return;
+        if (!reduce_f<3>(P, sc, fp, tp, epoch, parity))
+            return false;
         wc ^= 1;
         if (t0) {
             gamma_old = gamma;
@@ -569,17 +628,26 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
     __syncthreads();
     if (s_need) {
         double pt[2] = {0.0, 0.0}, tt[2];
-        residual64_pass<R, KB>(P, bh, xh, r, pt);
-        if (!reduce_d<2>(P, pt, tt, epoch, parity))
-            return;
+        residual64_pass<R, KB>(P, sc, bh, xh, r, pt);
+        if (!reduce_d<2>(P, sc, pt, tt, epoch, parity))
+            return false;
         if (t0) {
             ++reps;
             rho = tt[1];
         }
     }
-    unscale_pass<R>(P, xh);
+    unscale_pass<R>(P, sc, xh);
     if (t0)
-        write_out(P, status, it, reps, sqrt(rho / bn2), sqrt(bn2));
+        write_out(P, sc, status, it, reps, sqrt(rho / bn2), sqrt(bn2));
+    return true;
+}
+
+template <int R, int KB>
+__global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
+    if (P.fault_inject && blockIdx.x == 0)
+        return;   // test hook: this block never arrives at a barrier
+    const Scope sc = grid_scope(P);
+    pipe64_body<R, KB>(P, sc);
 }
 
 // ============================================================================
@@ -604,11 +672,10 @@ struct MixedState {
 };
 
 template <int R, int KB, bool DEFL>
-__global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
-    if (P.fault_inject && blockIdx.x == 0)
-        return;
+__device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc) {
+    __syncthreads();   // the previous body of this block is done with shared state
     LANE_ROWS;
-    load_slice_meta(P.A, range);
+    load_slice_meta(P.A, sc.range);
     const SellView &A = P.A;
     double *xh = P.v64[0], *bh = P.v64[1], *rt = P.v64[2], *w0 = P.v64[3], *q0 = P.v64[4];
     float *xc = P.v32[0], *r = P.v32[1], *wa = P.v32[2], *wb = P.v32[3];
@@ -621,18 +688,18 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
     int parity = 0, wc = 0;
 
     double b2[1] = {0.0}, t1[1];
-    prep_pass<R>(P, bh, xh, b2);
-    zero_rows<float, R>(P, xc);
-    zero_rows<float, R>(P, p);
-    zero_rows<float, R>(P, z);
-    zero_rows<float, R>(P, sv);
-    if (!reduce_d<1>(P, b2, t1, epoch, parity))
-        return;
+    prep_pass<R>(P, sc, bh, xh, b2);
+    zero_rows<float, R>(P, sc, xc);
+    zero_rows<float, R>(P, sc, p);
+    zero_rows<float, R>(P, sc, z);
+    zero_rows<float, R>(P, sc, sv);
+    if (!reduce_d<1>(P, sc, b2, t1, epoch, parity))
+        return false;
     const double bn2 = t1[0];
     if (bn2 == 0.0) {
-        zero_solution(P);
-        write_out(P, kDevOk, 0, 0, 0.0, 0.0);
-        return;
+        zero_solution(P, sc);
+        write_out(P, sc, kDevOk, 0, 0, 0.0, 0.0);
+        return true;
     }
     const double thr2 = P.tol * P.tol * bn2;
     double cW = 1.0;   // (w0, q0)
@@ -647,8 +714,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             for (int j = 0; j < R; ++j)
                 pd[0] += dd[j];
         }
-        if (!reduce_d<1>(P, pd, td, epoch, parity))
-            return;
+        if (!reduce_d<1>(P, sc, pd, td, epoch, parity))
+            return false;
         const double inv_norm = 1.0 / sqrt(td[0]);
         FOR_MY_SLICES(s) {
             const int row0 = s * A.C + R * lane;
@@ -663,8 +730,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             st_rows<R>(w0 + row0, ss);
             st_rows<R>(w0f + row0, sf);
         }
-        if (!grid_sync(P.sync, epoch))
-            return;
+        if (!scope_sync(sc, P.sync, epoch))
+            return false;
         double pc[1] = {0.0}, tc[1];
         FOR_MY_SLICES(s) {
             const int row0 = s * A.C + R * lane;
@@ -683,8 +750,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             st_rows<R>(q0 + row0, acc);
             st_rows<R>(q0f + row0, qf);
         }
-        if (!reduce_d<1>(P, pc, tc, epoch, parity))
-            return;
+        if (!reduce_d<1>(P, sc, pc, tc, epoch, parity))
+            return false;
         cW = tc[0];
         FOR_MY_SLICES(s) {
             const int row0 = s * A.C + R * lane;
@@ -697,8 +764,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                 tf[j] = (float)acc[j];
             st_rows<R>(t0f + row0, tf);
         }
-        if (!grid_sync(P.sync, epoch))
-            return;
+        if (!scope_sync(sc, P.sync, epoch))
+            return false;
     }
     __shared__ MixedState S;   // thread 0 only
     if (t0) {
@@ -738,8 +805,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                 st_rows<R>(xh + row0, xx);
                 st_rows<R>(xc + row0, zr);
             }
-            if (!grid_sync(P.sync, epoch))
-                return;
+            if (!scope_sync(sc, P.sync, epoch))
+                return false;
             // U2: FP64 true residual (deflated by the coarse correction), stored
             // in float in units of the current sigma
             const double inv_sigma = 1.0 / sig;   // power of two: exact
@@ -778,8 +845,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                     }
                     st_rows<R>(rt + row0, acc);
                 }
-                if (!reduce_d<1>(P, pw, tw, epoch, parity))
-                    return;
+                if (!reduce_d<1>(P, sc, pw, tw, epoch, parity))
+                    return false;
                 const double a0 = tw[0] / cW;   // every thread: same value, a few FP64 ops once
                 // U2b: x += a0 w0 ; r -= a0 q0 (own rows only)
                 FOR_MY_SLICES(s) {
@@ -803,8 +870,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                     st_rows<R>(r + row0, rf);
                 }
             }
-            if (!reduce_d<2>(P, part, tot, epoch, parity))
-                return;
+            if (!reduce_d<2>(P, sc, part, tot, epoch, parity))
+                return false;
             if (t0) {
                 ++S.reps;
                 S.rho = tot[1];
@@ -851,8 +918,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
                 st_rows<R>(w + row0, aw);
                 st_rows<R>(sv + row0, as);
             }
-            if (!grid_sync(P.sync, epoch))
-                return;
+            if (!scope_sync(sc, P.sync, epoch))
+                return false;
             // U4: z = Ahat s ; r *= f ; p *= pf ; gamma, delta (, eps)
             KahanF g0, g1, g2;
             FOR_MY_SLICES(s) {
@@ -884,8 +951,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             }
             FF fd[3] = {g0.ff(), g1.ff(), g2.ff()};
             double td[3];
-            if (!reduce_f<3>(P, fd, td, epoch, parity))
-                return;
+            if (!reduce_f<3>(P, sc, fd, td, epoch, parity))
+                return false;
             if (t0) {
                 S.gamma = td[0];
                 S.delta = td[1];
@@ -993,8 +1060,8 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
         }
         FF fp[3] = {g0.ff(), g1.ff(), g2.ff()};
         double tp[3];
-        if (!reduce_f<3>(P, fp, tp, epoch, parity))
-            return;
+        if (!reduce_f<3>(P, sc, fp, tp, epoch, parity))
+            return false;
         wc ^= 1;
         if (t0) {
             S.gamma = tp[0];
@@ -1004,9 +1071,18 @@ __global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
             ++S.since;
         }
     }
-    unscale_pass<R>(P, xh);
+    unscale_pass<R>(P, sc, xh);
     if (t0)
-        write_out(P, S.status, S.it, S.reps, sqrt(S.rho / bn2), sqrt(bn2));
+        write_out(P, sc, S.status, S.it, S.reps, sqrt(S.rho / bn2), sqrt(bn2));
+    return true;
+}
+
+template <int R, int KB, bool DEFL>
+__global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
+    if (P.fault_inject && blockIdx.x == 0)
+        return;   // test hook: this block never arrives at a barrier
+    const Scope sc = grid_scope(P);
+    mixed_body<R, KB, DEFL>(P, sc);
 }
 
 }  // namespace

@@ -38,6 +38,10 @@ class PcgOpts(ctypes.Structure):
                 ("deflate", ctypes.c_int)]
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("max_team", ctypes.c_int), ("team_work_scale", ctypes.c_double)]
+
+
 class LduSolveStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
                 ("replacements", ctypes.c_int), ("relres", ctypes.c_double),
@@ -92,6 +96,20 @@ def lib():
         L.pcg_solve_ldu_noalloc.argtypes = [i64, i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, d, i,
                                             pi, pd, _vp]
         L.pcg_solve_ldu_noalloc.restype = i
+        L.ldu_create_batched.argtypes = [i, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                         ctypes.POINTER(LduOpts), _vp, ctypes.POINTER(_vp)]
+        L.ldu_create_batched.restype = i
+        L.ldu_batch_schedule.argtypes = [_vp, ctypes.POINTER(BatchOpts), _vp]
+        L.ldu_batch_schedule.restype = i
+        L.ldu_batch_info.argtypes = [_vp, pi, pi, pi, pi]
+        L.ldu_batch_info.restype = i
+        L.pcg_solve_batched_async.argtypes = [_vp, _vp, _vp, d, i, i, ctypes.POINTER(PcgOpts), _vp]
+        L.pcg_solve_batched_async.restype = i
+        L.ldu_batch_results.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.ldu_batch_results.restype = i
+        L.pcg_solve_batched.argtypes = [_vp, _vp, _vp, d, i, i, ctypes.POINTER(PcgOpts), _vp, _vp,
+                                        _vp, _vp]
+        L.pcg_solve_batched.restype = i
         L.ldu_status_string.argtypes = [i]
         L.ldu_status_string.restype = ctypes.c_char_p
         for name in ("ldu_create", "ldu_update_values", "ldu_set_face_coeffs", "ldu_spmv",
@@ -279,3 +297,90 @@ def from_system(sys_, device="cuda", **opts):
                    t(sys_.diag, torch.float64), t(sys_.upper, torch.float64),
                    t(sys_.lower, torch.float64), **opts)
     return A
+
+
+# ---- batches ----------------------------------------------------------------
+
+def ldu_create_batched(sizes, face_counts, owner, neighbour, diag, upper, lower, slice_rows=0,
+                       block_threads=0, blocks_per_sm=0, stream=None):
+    """Batched handle from concatenated device arrays (face indices local to
+    their system).  sizes / face_counts: per-system cells and faces."""
+    import numpy as np
+    nsys = len(sizes)
+    n_h = np.ascontiguousarray(sizes, dtype=np.int64)
+    f_h = np.ascontiguousarray(face_counts, dtype=np.int64)
+    n_tot, f_tot = int(n_h.sum()), int(f_h.sum())
+    opts = LduOpts(slice_rows, block_threads, blocks_per_sm)
+    h = _vp()
+    st = lib().ldu_create_batched(
+        nsys, _vp(n_h.ctypes.data), _vp(f_h.ctypes.data), _dev(owner, torch.int32, f_tot, "owner"),
+        _dev(neighbour, torch.int32, f_tot, "neighbour"), _dev(diag, torch.float64, n_tot, "diag"),
+        _dev(upper, torch.float64, f_tot, "upper"), _dev(lower, torch.float64, f_tot, "lower"),
+        ctypes.byref(opts), _stream(stream), ctypes.byref(h))
+    _check(st, "ldu_create_batched", allow_not_converged=False)
+    A = LduMatrix(h, n_tot, f_tot, diag.device)
+    A.nsys = nsys
+    A.sizes = n_h.copy()
+    return A
+
+
+def from_systems(systems, device="cuda", **opts):
+    """Upload a list of ldu_cases.LduSystem and create one batched handle."""
+    import numpy as np
+    cat = lambda name, dt: torch.as_tensor(  # noqa: E731
+        np.concatenate([getattr(s_, name) for s_ in systems])).to(device=device, dtype=dt)
+    return ldu_create_batched([s_.n for s_ in systems], [s_.nfaces for s_ in systems],
+                              cat("owner", torch.int32), cat("neighbour", torch.int32),
+                              cat("diag", torch.float64), cat("upper", torch.float64),
+                              cat("lower", torch.float64), **opts)
+
+
+def ldu_batch_schedule(A, max_team=0, team_work_scale=0.0, stream=None):
+    o = BatchOpts(int(max_team), float(team_work_scale))
+    _check(lib().ldu_batch_schedule(A.handle, ctypes.byref(o), _stream(stream)),
+           "ldu_batch_schedule", allow_not_converged=False)
+
+
+def ldu_batch_info(A):
+    v = [ctypes.c_int(0) for _ in range(4)]
+    _check(lib().ldu_batch_info(A.handle, *[ctypes.byref(t) for t in v]), "ldu_batch_info")
+    return dict(zip(("nsys", "grid_blocks", "ntasks", "max_team"), (t.value for t in v)))
+
+
+def _pcg_opts(rr_period=0, tau=0.0, restart=False, deflate=False, barrier_timeout_s=0.0):
+    return PcgOpts(int(rr_period), float(tau), int(bool(restart)), float(barrier_timeout_s), 0,
+                   int(bool(deflate)))
+
+
+def pcg_solve_batched_async(A, b, x, tol=1e-8, maxit=20000, precision="mixed", stream=None,
+                            **opts):
+    """Queue the batched solve (no synchronisation; graph-capturable)."""
+    o = _pcg_opts(**opts)
+    st = lib().pcg_solve_batched_async(A.handle, _dev(b, torch.float64, A.n, "b"),
+                                       _dev(x, torch.float64, A.n, "x"), float(tol), int(maxit),
+                                       _PREC[precision], ctypes.byref(o), _stream(stream))
+    _check(st, "pcg_solve_batched_async", allow_not_converged=False)
+
+
+def ldu_batch_results(A, stream=None):
+    """(worst status, iters[nsys], relres[nsys], status[nsys]) of the last batched solve."""
+    import numpy as np
+    it = np.zeros(A.nsys, dtype=np.int32)
+    rr = np.zeros(A.nsys, dtype=np.float64)
+    stv = np.zeros(A.nsys, dtype=np.int32)
+    worst = lib().ldu_batch_results(A.handle, _vp(it.ctypes.data), _vp(rr.ctypes.data),
+                                    _vp(stv.ctypes.data), _stream(stream))
+    return worst, it, rr, stv
+
+
+def pcg_solve_batched(A, b, x=None, tol=1e-8, maxit=20000, precision="mixed", stream=None,
+                      check=True, **opts):
+    """Solve every system of a batched handle.  Returns
+    (x, worst status, iters[nsys], relres[nsys], status[nsys])."""
+    if x is None:
+        x = torch.zeros(A.n, dtype=torch.float64, device=b.device)
+    pcg_solve_batched_async(A, b, x, tol, maxit, precision, stream, **opts)
+    worst, it, rr, stv = ldu_batch_results(A, stream)
+    if check:
+        _check(worst, "pcg_solve_batched")
+    return x, worst, it, rr, stv
