@@ -256,6 +256,26 @@ def run_ours(args):
     achieved = alg_bytes / statistics.median(t_mixed) / 1e9
 
     extra = {}
+    def timed_generic(call, steps, warmup, prep=None):
+        for _ in range(warmup):
+            if prep:
+                prep()
+            call()
+        torch.cuda.synchronize(dev)
+        times = []
+        for _ in range(steps):
+            if prep:
+                prep()
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+        return times
+
     if not args.skip_fp64:
         t_defl, o_defl = timed(mixed_deflated, max(2, args.steps // 2), 1)
         t_pcg, o_pcg = timed(pcg64, max(2, args.steps // 2), 1)
@@ -290,6 +310,10 @@ def run_ours(args):
 
     t_e2e, _ = timed(e2e_step, args.steps, 1)
     e2e_s = statistics.mean(t_e2e)
+
+    batched = None
+    if not args.skip_batched:
+        batched = run_batched(args, dev, pkg, timed_fn=timed_generic)
 
     # CPU baseline: the oracle on this host, bounded sample, rank 0 only
     cpu = None
@@ -326,6 +350,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "batched": batched,
     }
     line.update(extra)
     if rank == 0:
@@ -333,6 +358,54 @@ def run_ours(args):
     A.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_batched(args, dev, pkg, timed_fn):
+    """512 uneven systems (cube sides uniform in 8..48), mixed precision to
+    1e-8: one persistent launch (autotuned layout and teams) against the same
+    solves as 512 separate calls."""
+    import numpy as np
+    import torch
+
+    import ldu_cases as lc
+    from paper_1505_07630_gb300 import autotune
+
+    systems = lc.config4(nsys=args.batch_systems)
+    best = autotune.tune_batched(systems, tol=TOL, rr_period=args.rr_period)
+    A = pkg.from_systems(systems, device=dev, slice_rows=best["slice_rows"])
+    pkg.ldu_batch_schedule(A, max_team=best["max_team"], team_work_scale=best["team_work_scale"])
+    b = torch.as_tensor(np.concatenate([s.b for s in systems]), device=dev)
+    x = torch.zeros_like(b)
+
+    def one_launch():
+        pkg.pcg_solve_batched(A, b, x, tol=TOL, precision="mixed", rr_period=args.rr_period)
+
+    t_batch = timed_fn(one_launch, max(2, args.steps // 2), 1, prep=x.zero_)
+    worst, its, rrs, sts = pkg.ldu_batch_results(A)
+    info = pkg.ldu_batch_info(A)
+    # the same solves, one call per system (handles built outside the timing)
+    offs = np.concatenate([[0], np.cumsum([s.n for s in systems])])
+    handles = [pkg.from_system(s, device=dev, slice_rows=best["slice_rows"]) for s in systems]
+    views = [(b[offs[k]:offs[k + 1]], x[offs[k]:offs[k + 1]]) for k in range(len(systems))]
+
+    def separate():
+        for Ak, (bk, xk) in zip(handles, views):
+            pkg.pipecg_solve(Ak, bk, xk, tol=TOL, precision="mixed", rr_period=args.rr_period)
+
+    t_sep = timed_fn(separate, 1, 1, prep=x.zero_)
+    for Ak in handles:
+        Ak.close()
+    alg = sum(bytes_mixed(s.n, s.nfaces, int(its[k]), int(its[k]) // args.rr_period + 2)
+              for k, s in enumerate(systems))
+    tb = statistics.median(t_batch)
+    A.close()
+    return {"systems": len(systems), "cells": int(offs[-1]), "one_launch_s": tb,
+            "separate_calls_s": statistics.median(t_sep), "speedup": statistics.median(t_sep) / tb,
+            "worst_status": int(worst), "max_iters": int(its.max()), "mean_iters": float(its.mean()),
+            "max_relres": float(rrs.max()), "alg_gbs": alg / tb / 1e9,
+            "tuned": {k: best[k] for k in ("slice_rows", "max_team", "team_work_scale")},
+            "grid_blocks": info["grid_blocks"], "teams_max": info["max_team"],
+            "ntasks": info["ntasks"]}
 
 
 def main():
@@ -348,6 +421,8 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--batch-systems", type=int, default=512)
     args = ap.parse_args()
     if args.warmup < 0 or args.steps < 1:
         ap.error("need steps >= 1")

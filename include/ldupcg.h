@@ -193,6 +193,12 @@ int pipecg_solve(const ldu_matrix *A, const double *b, double *x, double tol, in
 int ldu_face_grad(const ldu_matrix *A, const double *lambda, const double *x, double *dcoef,
                   ldu_stream_t stream);
 
+/* Gradient of a loss with respect to the boundary part of the diagonal of
+ * ldu_set_face_coeffs: ddiag[i] = -lambda[i] x[i] (device double arrays of
+ * the caller's cells).  Queued on stream. */
+int ldu_diag_grad(const ldu_matrix *A, const double *lambda, const double *x, double *ddiag,
+                  ldu_stream_t stream);
+
 /* Counters of the last solve (host struct filled from host memory; no sync). */
 int ldu_last_stats(const ldu_matrix *A, ldu_solve_stats *stats);
 
@@ -219,7 +225,9 @@ typedef struct batch_opts {
                                 above 1 gives smaller teams (default 1) */
 } batch_opts;
 
-/* Create a batched handle.
+/* Create a batched handle.  On a batched handle, ldu_update_values,
+ * ldu_set_face_coeffs, ldu_face_grad and ldu_diag_grad take their arrays in
+ * the caller's concatenated order; ldu_spmv returns UNSUPPORTED.
  *   nsys            number of systems (> 0)
  *   n, nFaces       host int64[nsys]: cells and internal faces of each system
  *   owner, neighbour, diag, upper, lower

@@ -43,10 +43,12 @@ def poisson_box(nx, ny=None, nz=None, seed=0, sub=0, diffusivity="unit", sigma=1
     else:
         raise ValueError(diffusivity)
     coef, extra = diffusion_coefficients(geo, k, dirichlet)
-    if rhs == "uniform":
+    if isinstance(rhs, str) and rhs == "uniform":
         b = rng.uniform(rng.stream_base(seed, "rhs", sub), n, -1.0, 1.0)
-    elif rhs == "zero":
+    elif isinstance(rhs, str) and rhs == "zero":
         b = np.zeros(n)
+    elif isinstance(rhs, str):
+        raise ValueError(rhs)
     else:
         b = np.asarray(rhs, dtype=np.float64)
     s = assemble(geo, coef, extra, b, name=name,

@@ -1,0 +1,68 @@
+"""Differentiable solve: x = A(c)^-1 b as a torch.autograd.Function.
+
+A is the finite-volume matrix of face coefficients c (upper = lower = -c_f,
+each c_f added to both adjacent diagonals) plus a fixed boundary part of the
+diagonal (see ldu_set_face_coeffs).  For a loss L(x), with A symmetric, the
+adjoint lambda solves A lambda = dL/dx with the same kernels as the forward
+solve, and
+    dL/db = lambda
+    dL/dc_f = -(lambda_o - lambda_n)(x_o - x_n)      (ldu_face_grad)
+    dL/d(diag_extra)_i = -lambda_i x_i               (ldu_diag_grad)
+The handle may be a batched handle: b, x, c and diag_extra are then the
+systems' arrays concatenated, and both solves are one batched launch.
+"""
+import torch
+
+from . import ldupcg
+
+
+def _solve(A, b, x, cfg):
+    if getattr(A, "nsys", None) is not None:
+        prec = "fp64" if cfg["precision"] in ("fp64", "pcg") else "mixed"
+        ldupcg.pcg_solve_batched(A, b, x, tol=cfg["tol"], maxit=cfg["maxit"], precision=prec,
+                                 check=cfg["check"], **cfg["kw"])
+    elif cfg["precision"] in ("fp64", "pcg"):
+        ldupcg.pcg_solve(A, b, x, tol=cfg["tol"], maxit=cfg["maxit"], check=cfg["check"])
+    elif cfg["precision"] == "pipe":
+        ldupcg.pipecg_solve(A, b, x, tol=cfg["tol"], maxit=cfg["maxit"], precision="fp64",
+                            check=cfg["check"], **cfg["kw"])
+    else:
+        ldupcg.pipecg_solve(A, b, x, tol=cfg["tol"], maxit=cfg["maxit"], precision="mixed",
+                            check=cfg["check"], **cfg["kw"])
+
+
+class LduSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, coef, diag_extra, b, A, cfg):
+        coef = coef.detach().contiguous()
+        diag_extra = diag_extra.detach().contiguous()
+        ldupcg.ldu_set_face_coeffs(A, coef, diag_extra)
+        x = torch.zeros_like(b)
+        if cfg.get("x0") is not None:
+            x.copy_(cfg["x0"])
+        _solve(A, b.detach().contiguous(), x, cfg)
+        ctx.save_for_backward(coef, diag_extra, x)
+        ctx.A = A
+        ctx.cfg = cfg
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        coef, diag_extra, x = ctx.saved_tensors
+        A = ctx.A
+        # the handle may have been re-valued by another forward since
+        ldupcg.ldu_set_face_coeffs(A, coef, diag_extra)
+        lam = torch.zeros_like(x)
+        _solve(A, gx.detach().contiguous(), lam, ctx.cfg)
+        g_coef = ldupcg.ldu_face_grad(A, lam, x) if ctx.needs_input_grad[0] else None
+        g_extra = ldupcg.ldu_diag_grad(A, lam, x) if ctx.needs_input_grad[1] else None
+        g_b = lam if ctx.needs_input_grad[2] else None
+        return g_coef, g_extra, g_b, None, None
+
+
+def ldu_solve(A, coef, diag_extra, b, precision="fp64", tol=1e-12, maxit=100000, x0=None,
+              check=True, **kw):
+    """x = A(coef, diag_extra)^-1 b, differentiable in coef, diag_extra and b.
+    precision: 'fp64' (Jacobi-PCG), 'pipe' (FP64 pipelined) or 'mixed'."""
+    cfg = dict(precision=precision, tol=tol, maxit=maxit, x0=x0, check=check, kw=kw)
+    return LduSolve.apply(coef, diag_extra, b, A, cfg)

@@ -86,6 +86,8 @@ struct ldu_matrix {
     int device;
     int num_sms;
     int64_t n, nf, n_pad, nnz_pad, n_slices;
+    int64_t n_cells;           // caller's cells (n for a single system; without padding rows for a batch)
+    int *row_cell;             // batched handles: caller cell of each row, -1 between systems
     int C;
     int max_w;
     int block_threads;

@@ -112,7 +112,7 @@ void free_handle(ldu_matrix *A) {
     ldu::free_batch(A);
     void *ptrs[] = {A->slice_ptr, A->slice_w, A->col, A->fid, A->owner, A->neighbour,
                     A->val64, A->sd, A->isd, A->dg, A->val32, A->slots, A->bar_count,
-                    A->bar_err, A->out_dev, A->flags_dev};
+                    A->bar_err, A->out_dev, A->flags_dev, A->row_cell};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -131,7 +131,7 @@ int values_from_arrays(ldu_matrix *A, const double *diag, const double *up, cons
                        cudaStream_t st) {
     const int T = 256;
     k_diag_scale<<<blocks_for(A->n_pad, T), T, 0, st>>>((int)A->n, (int)A->n_pad, diag, A->sd,
-                                                        A->isd, A->dg, A->flags_dev);
+                                                        A->isd, A->dg, A->flags_dev, A->row_cell);
     k_values<<<blocks_for(A->n_pad, T), T, 0, st>>>((int)A->n_pad, A->C, A->slice_ptr, A->slice_w,
                                                     A->col, A->fid, up, lo, nullptr, A->sd,
                                                     A->val64, A->val32);
@@ -198,6 +198,7 @@ int ldu_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *neigh
     CK(cudaGetDevice(&A->device));
     CK(cudaDeviceGetAttribute(&A->num_sms, cudaDevAttrMultiProcessorCount, A->device));
     A->n = n;
+    A->n_cells = n;
     A->nf = nf;
     A->C = C;
     A->block_threads = bt;
@@ -355,7 +356,7 @@ int ldu_set_face_coeffs(ldu_matrix *A, const double *coef, const double *diag_ex
     const int T = 256;
     k_diag_from_coef<<<blocks_for(A->n_pad, T), T, 0, st>>>(
         (int)A->n, (int)A->n_pad, A->C, A->slice_ptr, A->slice_w, A->fid, coef, diag_extra, A->sd,
-        A->isd, A->dg, A->flags_dev);
+        A->isd, A->dg, A->flags_dev, A->row_cell);
     k_values<<<blocks_for(A->n_pad, T), T, 0, st>>>((int)A->n_pad, A->C, A->slice_ptr, A->slice_w,
                                                     A->col, A->fid, nullptr, nullptr, coef, A->sd,
                                                     A->val64, A->val32);
@@ -365,6 +366,8 @@ int ldu_set_face_coeffs(ldu_matrix *A, const double *coef, const double *diag_ex
 int ldu_spmv(const ldu_matrix *A, int precision, const void *x, void *y, ldu_stream_t stream) {
     if (!A || (A->n > 0 && (!x || !y)))
         return LDU_ERR_BAD_ARG;
+    if (A->row_cell)
+        return LDU_ERR_UNSUPPORTED;   // batched handles: solves and gradients only
     if (A->n == 0)
         return LDU_OK;
     cudaStream_t st = (cudaStream_t)stream;
@@ -391,6 +394,17 @@ int ldu_face_grad(const ldu_matrix *A, const double *lambda, const double *x, do
     k_face_grad<<<blocks_for(A->nf, 256), 256, 0, (cudaStream_t)stream>>>(A->nf, A->owner,
                                                                           A->neighbour, lambda, x,
                                                                           dcoef);
+    return cuda_status(cudaGetLastError());
+}
+
+int ldu_diag_grad(const ldu_matrix *A, const double *lambda, const double *x, double *ddiag,
+                  ldu_stream_t stream) {
+    if (!A || (A->n_cells > 0 && (!lambda || !x || !ddiag)))
+        return LDU_ERR_BAD_ARG;
+    if (A->n_cells == 0)
+        return LDU_OK;
+    k_diag_grad<<<blocks_for(A->n_cells, 256), 256, 0, (cudaStream_t)stream>>>(A->n_cells, lambda,
+                                                                             x, ddiag);
     return cuda_status(cudaGetLastError());
 }
 

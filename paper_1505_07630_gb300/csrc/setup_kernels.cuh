@@ -118,14 +118,17 @@ __global__ void k_sort_rows(int n, int C, const int *slice_ptr, const int *deg, 
     }
 }
 
-// diagonal scaling factors; padded rows get sd = isd = 1, dg = 0
+// diagonal scaling factors; padded rows get sd = isd = 1, dg = 0.  With a
+// row map (batched handles) diag is in the caller's cell order and rows
+// between systems (map -1) keep a unit diagonal.
 __global__ void k_diag_scale(int n, int n_pad, const double *diag, double *sd, double *isd,
-                             double *dg, int *flags) {
+                             double *dg, int *flags, const int *row_cell) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad)
         return;
     if (r < n) {
-        const double d = diag[r];
+        const int c = row_cell ? row_cell[r] : r;
+        const double d = c >= 0 ? diag[c] : 1.0;
         if (!(d > 0.0) || !isfinite(d))
             atomicOr(flags, kFlagBadDiag);
         const double q = sqrt(d);
@@ -140,9 +143,11 @@ __global__ void k_diag_scale(int n, int n_pad, const double *diag, double *sd, d
 }
 
 // diag[r] = extra[r] + sum of coef over the row's faces, in slot order
+// (extra in the caller's cell order when a row map is given)
 __global__ void k_diag_from_coef(int n, int n_pad, int C, const int *slice_ptr, const int *slice_w,
                                  const uint32_t *fid, const double *coef, const double *extra,
-                                 double *sd, double *isd, double *dg, int *flags) {
+                                 double *sd, double *isd, double *dg, int *flags,
+                                 const int *row_cell) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad)
         return;
@@ -154,7 +159,8 @@ __global__ void k_diag_from_coef(int n, int n_pad, int C, const int *slice_ptr, 
     }
     const int s = r / C, i = r - s * C;
     const int w = slice_w[s];
-    double d = extra[r];
+    const int c = row_cell ? row_cell[r] : r;
+    double d = c >= 0 ? extra[c] : 1.0;
     for (int k = 0; k < w; ++k) {
         const uint32_t f = fid[slice_ptr[s] + k * C + i];
         if (f != kPadFid)
@@ -212,6 +218,14 @@ __global__ void k_spmv(int n, int C, const int *slice_ptr, const int *slice_w, c
             acc = fma(val[at], (T)sd[c] * x[c], acc);
     }
     y[r] = sr * acc;
+}
+
+// dL/d(diag_extra)_i = -lambda_i x_i (the diagonal enters A as +e_i e_i^T)
+__global__ void k_diag_grad(int64_t n, const double *__restrict__ lam,
+                            const double *__restrict__ x, double *__restrict__ g) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        g[i] = -lam[i] * x[i];
 }
 
 __global__ void k_face_grad(int64_t nf, const int32_t *__restrict__ own,

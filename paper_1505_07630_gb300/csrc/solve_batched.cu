@@ -104,6 +104,44 @@ __global__ void k_batch_faces(int64_t nf, int nsys, const int64_t *f_off, const 
     }
 }
 
+// after the repack: the handle keeps face addressing and a row map in the
+// caller's cell numbering (system offset + local index), for the value
+// setters and the gradients
+__global__ void k_batch_remap(int64_t nf, int nsys, const int64_t *f_off, const int64_t *b_off,
+                              const int32_t *own, const int32_t *nbr, int32_t *own_h,
+                              int32_t *nbr_h) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nsys - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (f_off[mid] <= f)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        own_h[f] = (int32_t)(own[f] + b_off[lo]);
+        nbr_h[f] = (int32_t)(nbr[f] + b_off[lo]);
+    }
+}
+
+__global__ void k_batch_rowmap(int64_t rows, int nsys, const int64_t *row0, const int64_t *n,
+                               const int64_t *b_off, int *row_cell) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = nsys - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row0[mid] <= r)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int64_t i = r - row0[lo];
+        row_cell[r] = i < n[lo] ? (int)(b_off[lo] + i) : -1;
+    }
+}
+
 __global__ void k_batch_diag(int64_t rows, int nsys, const int64_t *row0, const int64_t *n,
                              const int64_t *b_off, const double *diag, double *diag_c) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows;
@@ -372,6 +410,16 @@ int ldu_create_batched(int nsys, const int64_t *n, const int64_t *nFaces, const 
     rc = ldu_create(rows, faces, own_c, nbr_c, diag_c, upper, lower, opt, stream, &A);
     if (rc != LDU_OK)
         goto fail;
+    // caller numbering for the setters and gradients
+    CKB(cudaMalloc((void **)&A->row_cell, sizeof(int) * std::max<int64_t>(rows, 1)));
+    if (faces > 0)
+        k_batch_remap<<<blocks_of(faces, 256), 256, 0, st>>>(faces, nsys, tab, tab + 3 * nsys, owner,
+                                                              neighbour, A->owner, A->neighbour);
+    k_batch_rowmap<<<blocks_of(rows, 256), 256, 0, st>>>(rows, nsys, tab + nsys, tab + 2 * nsys,
+                                                        tab + 3 * nsys, A->row_cell);
+    CKB(cudaGetLastError());
+    CKB(cudaStreamSynchronize(st));
+    A->n_cells = cells;
     {
         std::vector<SysDev> sys(nsys);
         for (int k = 0; k < nsys; ++k)

@@ -89,6 +89,8 @@ def lib():
         L.pcg_solve.argtypes = [_vp, _vp, _vp, d, i, pi, pd, _vp]
         L.pipecg_solve.argtypes = [_vp, _vp, _vp, d, i, i, ctypes.POINTER(PcgOpts), pi, pd, _vp]
         L.ldu_face_grad.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.ldu_diag_grad.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.ldu_diag_grad.restype = i
         L.ldu_last_stats.argtypes = [_vp, ctypes.POINTER(LduSolveStats)]
         L.ldu_get_info.argtypes = [_vp, ctypes.POINTER(LduInfo)]
         L.ldu_destroy.argtypes = [_vp]
@@ -284,6 +286,17 @@ def pcg_solve_ldu_noalloc(n, owner, neighbour, diag, upper, lower, b, x, tol=1e-
     if check:
         _check(st, "pcg_solve_ldu_noalloc")
     return x, st, it.value, rr.value
+
+
+def ldu_diag_grad(A, lam, x, out=None, stream=None):
+    """dL/d(diag_extra) = -lambda * x in the library's kernel."""
+    if out is None:
+        out = torch.empty(A.n, dtype=torch.float64, device=x.device)
+    st = lib().ldu_diag_grad(A.handle, _dev(lam, torch.float64, A.n, "lambda"),
+                             _dev(x, torch.float64, A.n, "x"),
+                             _dev(out, torch.float64, A.n, "ddiag"), _stream(stream))
+    _check(st, "ldu_diag_grad", allow_not_converged=False)
+    return out
 
 
 def ldu_destroy(A):

@@ -1,0 +1,137 @@
+"""Differentiable solve: autograd gradients of L = 0.5 ||x(c, b) - x_t||^2
+against the oracle's adjoint gradient and against central finite
+differences of the loss.
+
+Tolerances: gradients from the oracle's dense LU adjoint within 1e-8
+(relative, tight solves); full-size members within 1e-6 of the oracle's
+PCG adjoint; finite differences (h = 1e-6, loss difference formed as
+0.5 sum (x+ - x-)(x+ + x- - 2 x_t) to avoid cancellation) within relative
+1e-5, floor 1e-5 * max |grad|."""
+import numpy as np
+import pytest
+
+import ldu_cases as lc
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_1505_07630_gb300 as p
+    return p
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "pipe", "mixed"])
+def test_gradients_match_oracle_adjoint(pkg, oracle_mod, precision):
+    s = lc.poisson_box(6, 5, 4, diffusivity="lognormal", seed=3)
+    A = pkg.from_system(s)
+    xt = np.random.default_rng(0).uniform(-1, 1, s.n)
+    coef = dev(s.coef).requires_grad_(True)
+    extra = dev(s.diag_extra).requires_grad_(True)
+    b = dev(s.b).requires_grad_(True)
+    x = pkg.ldu_solve(A, coef, extra, b, precision=precision, tol=1e-13)
+    loss = 0.5 * ((x - dev(xt)) ** 2).sum()
+    loss.backward()
+    d, u, lo = oracle_mod.matrix_from_coef(s, s.coef)
+    M = oracle_mod.dense(s, d, u, lo)
+    x_o = oracle_mod.lu_solve(M, s.b)
+    lam = oracle_mod.lu_solve(M.T, x_o - xt)
+    g_c = oracle_mod.face_grad(s.owner, s.neighbour, lam, x_o)
+    for got, ref in ((coef.grad, g_c), (extra.grad, -lam * x_o), (b.grad, lam)):
+        got = got.cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref), precision
+    A.close()
+
+
+def test_finite_differences_small(pkg):
+    s = lc.poisson_box(5, 4, 6, diffusivity="lognormal", seed=8)
+    A = pkg.from_system(s)
+    xt = dev(np.random.default_rng(1).uniform(-1, 1, s.n))
+    coef = dev(s.coef).requires_grad_(True)
+    b = dev(s.b).requires_grad_(True)
+    extra = dev(s.diag_extra)
+    x = pkg.ldu_solve(A, coef, extra, b, tol=1e-14)
+    (0.5 * ((x - xt) ** 2).sum()).backward()
+    h = 1e-6
+    rng = np.random.default_rng(2)
+
+    def dloss(c, bb):
+        with torch.no_grad():
+            xp = pkg.ldu_solve(A, c[0], extra, bb[0], tol=1e-14, x0=x, check=False)
+            xm = pkg.ldu_solve(A, c[1], extra, bb[1], tol=1e-14, x0=x, check=False)
+            return float(0.5 * ((xp - xm) * (xp + xm - 2 * xt)).sum()) / (2 * h)
+
+    gc = coef.grad.cpu().numpy()
+    for f in rng.choice(s.nfaces, 10, replace=False):
+        cp, cm = coef.detach().clone(), coef.detach().clone()
+        cp[f] += h
+        cm[f] -= h
+        fd = dloss((cp, cm), (b.detach(), b.detach()))
+        assert abs(fd - gc[f]) <= 1e-5 * max(abs(gc[f]), np.abs(gc).max()), (f, fd, gc[f])
+    gb = b.grad.cpu().numpy()
+    for i in rng.choice(s.n, 10, replace=False):
+        bp, bm = b.detach().clone(), b.detach().clone()
+        bp[i] += h
+        bm[i] -= h
+        fd = dloss((coef.detach(), coef.detach()), (bp, bm))
+        assert abs(fd - gb[i]) <= 1e-5 * max(abs(gb[i]), np.abs(gb).max()), (i, fd, gb[i])
+    A.close()
+
+
+def test_config5_batch_of_8(pkg, oracle_mod):
+    """64^3 mesh, batch of 8 lognormal fields, targets from a reference field
+    (oracle solves), one batched handle for forward and adjoint; oracle
+    adjoint on two members; finite differences on 20 faces and 20 RHS
+    entries of the whole batch."""
+    systems, refs = lc.config5()
+    A = pkg.from_systems(systems)
+    xt_np = [oracle_mod.pcg(r, tol=1e-10).x for r in refs]
+    xt = dev(np.concatenate(xt_np))
+    coef = dev(np.concatenate([s.coef for s in systems])).requires_grad_(True)
+    extra = dev(np.concatenate([s.diag_extra for s in systems]))
+    b = dev(np.concatenate([s.b for s in systems])).requires_grad_(True)
+    x = pkg.ldu_solve(A, coef, extra, b, tol=1e-13)
+    (0.5 * ((x - xt) ** 2).sum()).backward()
+    gc = coef.grad.cpu().numpy()
+    gb = b.grad.cpu().numpy()
+    n, F = systems[0].n, systems[0].nfaces
+    for m in (0, 5):
+        s = systems[m]
+        xo = oracle_mod.pcg(s, tol=1e-13).x
+        lam = oracle_mod.pcg(s, b=xo - xt_np[m], tol=1e-13).x
+        ref_c = oracle_mod.face_grad(s.owner, s.neighbour, lam, xo)
+        got_c = gc[m * F:(m + 1) * F]
+        assert np.linalg.norm(got_c - ref_c) <= 1e-6 * np.linalg.norm(ref_c), m
+        got_b = gb[m * n:(m + 1) * n]
+        assert np.linalg.norm(got_b - lam) <= 1e-6 * np.linalg.norm(lam), m
+    h = 1e-6
+    rng = np.random.default_rng(5)
+
+    def dloss(c, bb):
+        with torch.no_grad():
+            xp = pkg.ldu_solve(A, c[0], extra, bb[0], tol=1e-14, x0=x, check=False)
+            xm = pkg.ldu_solve(A, c[1], extra, bb[1], tol=1e-14, x0=x, check=False)
+            return float(0.5 * ((xp - xm) * (xp + xm - 2 * xt)).sum()) / (2 * h)
+
+    for f in rng.choice(coef.numel(), 20, replace=False):
+        cp, cm = coef.detach().clone(), coef.detach().clone()
+        cp[f] += h
+        cm[f] -= h
+        fd = dloss((cp, cm), (b.detach(), b.detach()))
+        assert abs(fd - gc[f]) <= 1e-5 * max(abs(gc[f]), np.abs(gc).max()), (f, fd, gc[f])
+    for i in rng.choice(b.numel(), 20, replace=False):
+        bp, bm = b.detach().clone(), b.detach().clone()
+        bp[i] += h
+        bm[i] -= h
+        fd = dloss((coef.detach(), coef.detach()), (bp, bm))
+        assert abs(fd - gb[i]) <= 1e-5 * max(abs(gb[i]), np.abs(gb).max()), (i, fd, gb[i])
+    A.close()
