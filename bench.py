@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -39,6 +40,42 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# ---- ncu traffic of the dominant kernel ----------------------------------------
+PROFILE = os.path.join(ROOT, "profiles", "k_mixed_poisson128.md")
+
+
+def source_digest():
+    """sha256 over the library's CUDA sources and header: a profile's DRAM
+    counters describe the kernel only while this digest is unchanged."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_1505_07630_gb300", "csrc", "*.cu*"))
+                   + glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """(dram bytes per launch, iterations) from the committed ncu summary, or
+    None when the kernel sources changed since that capture."""
+    try:
+        fields = {}
+        with open(PROFILE) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    fields[k.strip()] = v.strip().strip("`")
+        if fields.get("source_sha256") != source_digest():
+            return None
+        return float(fields["dram_bytes_per_launch"]), int(fields["iterations"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 # ---- algorithmic bytes (one launch = one solve) ------------------------------
@@ -81,7 +118,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"ldupcg_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -254,6 +291,10 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     alg_bytes = bytes_mixed(n, F, it, reps)
     achieved = alg_bytes / statistics.median(t_mixed) / 1e9
+    prof = profiled_traffic()
+    traffic = None
+    if prof is not None and prof[1] == it:
+        traffic = prof[0]
 
     extra = {}
     def timed_generic(call, steps, warmup, prep=None):
@@ -342,7 +383,7 @@ def run_ours(args):
         "solve": {"status": st, "iters": it, "replacements": reps, "relres": rr,
                   "relres_oracle": relres_oracle},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "k_mixed (persistent, one launch per solve)",
                      "alg_bytes_per_launch": alg_bytes},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n,
@@ -423,7 +464,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--batch-systems", type=int, default=512)
+    ap.add_argument("--print-digest", action="store_true")
     args = ap.parse_args()
+    if args.print_digest:
+        print(source_digest())
+        return
     if args.warmup < 0 or args.steps < 1:
         ap.error("need steps >= 1")
     if args.impl == "reference":
