@@ -228,9 +228,28 @@ def run_ours(args):
     __graft_entry__.build()
     import paper_1505_07630_gb300 as pkg
 
+    from paper_1505_07630_gb300 import autotune
+
     s = lc.config2(s=args.size, seed=0)
     n, F = s.n, s.nfaces
-    A = pkg.from_system(s, device=dev, slice_rows=args.slice_rows, block_threads=args.block_threads)
+    # each solver at its own best layout (autotuned once, cached; untimed)
+    cands = (args.slice_rows,) if args.slice_rows else (64, 128)
+    fixed = {"rr_period": args.rr_period} if args.rr_period else {}
+    if args.slice_rows and args.rr_period:
+        tune_m = {"slice_rows": args.slice_rows, "rr_period": args.rr_period}   # fixed: no tuning
+    else:
+        tune_m = autotune.tune_single(s, "mixed", tol=TOL, slice_rows=cands, **fixed)
+    rr_m = args.rr_period or tune_m.get("rr_period", 12)
+    handles = {}
+
+    def handle(C):
+        if C not in handles:
+            handles[C] = pkg.from_system(s, device=dev, slice_rows=C,
+                                         block_threads=args.block_threads,
+                                         blocks_per_sm=args.blocks_per_sm, staging=args.staging)
+        return handles[C]
+
+    A = handle(tune_m["slice_rows"])
     b = torch.as_tensor(s.b, device=dev)
     x = torch.zeros(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -256,22 +275,26 @@ def run_ours(args):
         return times, outs
 
     def mixed():
-        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="mixed",
-                                         rr_period=args.rr_period)
+        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="mixed", rr_period=rr_m)
         return st, it, rr, A.stats()["replacements"]
 
     def mixed_deflated():
-        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="mixed",
-                                         rr_period=args.rr_period, deflate=True)
+        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="mixed", rr_period=rr_m,
+                                         deflate=True)
         return st, it, rr, A.stats()["replacements"]
+
+    A_pcg = A_pipe = A
+    if not args.skip_fp64:
+        A_pcg = handle(autotune.tune_single(s, "pcg", tol=TOL, slice_rows=cands)["slice_rows"])
+        A_pipe = handle(autotune.tune_single(s, "fp64", tol=TOL, slice_rows=cands)["slice_rows"])
 
     def pcg64():
-        _, st, it, rr = pkg.pcg_solve(A, b, x, tol=TOL)
-        return st, it, rr, A.stats()["replacements"]
+        _, st, it, rr = pkg.pcg_solve(A_pcg, b, x, tol=TOL)
+        return st, it, rr, A_pcg.stats()["replacements"]
 
     def pipe64():
-        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="fp64")
-        return st, it, rr, A.stats()["replacements"]
+        _, st, it, rr = pkg.pipecg_solve(A_pipe, b, x, tol=TOL, precision="fp64")
+        return st, it, rr, A_pipe.stats()["replacements"]
 
     if dist is not None:
         dist.barrier()
@@ -330,8 +353,10 @@ def run_ours(args):
             "mixed_deflated": {"s": statistics.median(t_defl), "iters": dit, "relres": drr,
                                "status": dst, "replacements": dreps},
             "fp64_pcg": {"s": mp, "iters": pit, "relres": prr, "status": pst,
+                         "slice_rows": A_pcg.info()["slice_rows"],
                          "alg_gbs": bytes_pcg64(n, F, pit, preps) / mp / 1e9},
             "fp64_pipecg": {"s": mq, "iters": qit, "relres": qrr, "status": qst,
+                            "slice_rows": A_pipe.info()["slice_rows"],
                             "alg_gbs": bytes_pipe64(n, F, qit, qreps) / mq / 1e9},
             "speedup_mixed_vs_fp64_pcg": mp / statistics.median(t_mixed),
         }
@@ -345,7 +370,7 @@ def run_ours(args):
     def e2e_step():
         bd.copy_(hb, non_blocking=True)
         x.zero_()
-        pkg.pipecg_solve(A, bd, x, tol=TOL, precision="mixed", rr_period=args.rr_period)
+        pkg.pipecg_solve(A, bd, x, tol=TOL, precision="mixed", rr_period=rr_m)
         hx.copy_(x, non_blocking=True)
         return None
 
@@ -377,8 +402,9 @@ def run_ours(args):
         "config": {"workload": f"poisson {args.size}^3 lognormal(0,1) k, harmonic faces, random+RCM "
                                "order, Dirichlet x-walls; mixed pipelined Jacobi-PCG to 1e-8",
                    "cells": n, "faces": F, "slice_rows": A.info()["slice_rows"],
+                   "blocks_per_sm": args.blocks_per_sm, "staging": args.staging,
                    "grid_blocks": grid["grid_blocks"], "block_threads": grid["block_threads"],
-                   "rr_period": args.rr_period, "l2": "256 MB flush before every step",
+                   "rr_period": rr_m, "l2": "256 MB flush before every step",
                    "parallelism": "replicas" if world > 1 else "single"},
         "solve": {"status": st, "iters": it, "replacements": reps, "relres": rr,
                   "relres_oracle": relres_oracle},
@@ -396,7 +422,8 @@ def run_ours(args):
     line.update(extra)
     if rank == 0:
         print(json.dumps(line))
-    A.close()
+    for h in handles.values():
+        h.close()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -412,14 +439,15 @@ def run_batched(args, dev, pkg, timed_fn):
     from paper_1505_07630_gb300 import autotune
 
     systems = lc.config4(nsys=args.batch_systems)
-    best = autotune.tune_batched(systems, tol=TOL, rr_period=args.rr_period)
+    rr_b = args.rr_period or 12
+    best = autotune.tune_batched(systems, tol=TOL, rr_period=rr_b)
     A = pkg.from_systems(systems, device=dev, slice_rows=best["slice_rows"])
     pkg.ldu_batch_schedule(A, max_team=best["max_team"], team_work_scale=best["team_work_scale"])
     b = torch.as_tensor(np.concatenate([s.b for s in systems]), device=dev)
     x = torch.zeros_like(b)
 
     def one_launch():
-        pkg.pcg_solve_batched(A, b, x, tol=TOL, precision="mixed", rr_period=args.rr_period)
+        pkg.pcg_solve_batched(A, b, x, tol=TOL, precision="mixed", rr_period=rr_b)
 
     t_batch = timed_fn(one_launch, max(2, args.steps // 2), 1, prep=x.zero_)
     worst, its, rrs, sts = pkg.ldu_batch_results(A)
@@ -431,12 +459,12 @@ def run_batched(args, dev, pkg, timed_fn):
 
     def separate():
         for Ak, (bk, xk) in zip(handles, views):
-            pkg.pipecg_solve(Ak, bk, xk, tol=TOL, precision="mixed", rr_period=args.rr_period)
+            pkg.pipecg_solve(Ak, bk, xk, tol=TOL, precision="mixed", rr_period=rr_b)
 
     t_sep = timed_fn(separate, 1, 1, prep=x.zero_)
     for Ak in handles:
         Ak.close()
-    alg = sum(bytes_mixed(s.n, s.nfaces, int(its[k]), int(its[k]) // args.rr_period + 2)
+    alg = sum(bytes_mixed(s.n, s.nfaces, int(its[k]), int(its[k]) // rr_b + 2)
               for k, s in enumerate(systems))
     tb = statistics.median(t_batch)
     A.close()
@@ -458,7 +486,9 @@ def main():
     ap.add_argument("--size", type=int, default=128)
     ap.add_argument("--slice-rows", type=int, default=0)
     ap.add_argument("--block-threads", type=int, default=0)
-    ap.add_argument("--rr-period", type=int, default=16)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--staging", type=int, default=0, choices=[0, -1])
+    ap.add_argument("--rr-period", type=int, default=0)
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

@@ -65,7 +65,14 @@ typedef struct ldu_opts {
     int block_threads;  /* threads per block of the persistent solve kernels:
                            128 or 256 (default 256) */
     int blocks_per_sm;  /* resident blocks per SM for the persistent kernels;
-                           0 = as many as fit */
+                           0 = as many as fit.  The mixed solve also has
+                           builds with fewer registers per thread for 3
+                           (slice_rows 32 or 64) and 4 (slice_rows 32)
+                           blocks per SM, chosen by this field */
+    int staging;        /* float sweeps of the mixed solve: 0 = stage each
+                           warp's next matrix slice into shared memory with
+                           bulk copies when it fits (default), -1 = read the
+                           matrix with plain loads */
 } ldu_opts;
 
 /* Options of pipecg_solve (and pcg_solve_batched).  NULL or zeroed selects
@@ -74,7 +81,7 @@ typedef struct pcg_opts {
     int rr_period;          /* iterations between residual replacements:
                                LDU_FP64 default 0 (replace only when the
                                recursive residual reaches tol);
-                               LDU_MIXED default 16 (FP64 replacement) */
+                               LDU_MIXED default 12 (FP64 replacement) */
     double tau;             /* LDU_MIXED: also replace when (r, M^-1 r) has
                                dropped by tau^2 since the last replacement;
                                0 = off (default) */

@@ -119,7 +119,7 @@ def pipecg(s, b=None, x0=None, tol=1e-8, maxit=20000, rr_period=0, history=False
     return Result(x, st, it.value, rr.value, hist)
 
 
-def mixed_pipecg(s, b=None, x0=None, tol=1e-8, period=16, tau=0.0, restart=False,
+def mixed_pipecg(s, b=None, x0=None, tol=1e-8, period=12, tau=0.0, restart=False,
                  maxit=20000, deflate=False):
     """FP32 pipelined Jacobi-PCG with FP64 residual replacement every `period`
     iterations (and when gamma dropped by tau^2, or convergence is predicted);

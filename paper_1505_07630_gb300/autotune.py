@@ -67,27 +67,41 @@ def _time(call, repeats):
     return best
 
 
-def tune_single(system, precision="mixed", tol=1e-8, repeats=2, use_cache=True, **solve_kw):
-    """Best slice height for pipecg_solve / pcg_solve on this system."""
-    key = _key("single", [system.n], [system.nfaces], dict(precision=precision, tol=tol, **solve_kw))
+RR_PERIODS = (12, 16)
+
+
+def tune_single(system, precision="mixed", tol=1e-8, repeats=2, use_cache=True,
+                slice_rows=SLICE_ROWS, **solve_kw):
+    """Best slice height (and, for the mixed solve, replacement period) for
+    pcg_solve ('pcg') / pipecg_solve ('fp64', 'mixed') on this system."""
+    key = _key("single", [system.n], [system.nfaces],
+               dict(precision=precision, tol=tol, slice_rows=list(slice_rows), **solve_kw))
     if use_cache:
         hit = _load().get(key)
         if hit:
             return hit
     b = torch.as_tensor(system.b, device="cuda")
     x = torch.zeros_like(b)
+    periods = RR_PERIODS if precision == "mixed" and "rr_period" not in solve_kw else (None,)
     results = []
-    for C in SLICE_ROWS:
+    for C in slice_rows:
         A = ldupcg.from_system(system, slice_rows=C)
+        for rr in periods:
+            kw = dict(solve_kw)
+            if rr is not None:
+                kw["rr_period"] = rr
 
-        def call():
-            x.zero_()
-            if precision == "pcg":
-                ldupcg.pcg_solve(A, b, x, tol=tol)
-            else:
-                ldupcg.pipecg_solve(A, b, x, tol=tol, precision=precision, **solve_kw)
+            def call():
+                x.zero_()
+                if precision == "pcg":
+                    ldupcg.pcg_solve(A, b, x, tol=tol)
+                else:
+                    ldupcg.pipecg_solve(A, b, x, tol=tol, precision=precision, **kw)
 
-        results.append({"slice_rows": C, "seconds": _time(call, repeats)})
+            res = {"slice_rows": C, "seconds": _time(call, repeats)}
+            if rr is not None:
+                res["rr_period"] = rr
+            results.append(res)
         A.close()
     best = min(results, key=lambda r: r["seconds"])
     best = dict(best, candidates=results)

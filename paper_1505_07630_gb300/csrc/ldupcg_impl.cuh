@@ -69,6 +69,9 @@ struct SellView {
     const double *isd;      // [n_pad]
     const double *dg;       // [n_pad]
     int meta_smem;          // 1: each block keeps its slices' (offset, width) in shared memory
+    int meta_cap;           // slice entries reserved for that metadata in shared memory
+    int stage_w;            // > 0: float sweeps stage (col, val32) slices of width <= stage_w
+                            // into shared memory with bulk copies; 0: plain global loads
 };
 
 // Barrier state shared by the blocks of one persistent launch.
@@ -92,6 +95,7 @@ struct ldu_matrix {
     int max_w;
     int block_threads;
     int blocks_per_sm;
+    int staging;               // 0 auto, -1 off
     int64_t device_bytes;
     // structure
     int *slice_ptr, *slice_w, *col;
@@ -121,6 +125,7 @@ int cuda_status(cudaError_t e);
 int launch_persistent(const void *kernel, int grid, int block, void **args, size_t smem,
                       cudaStream_t s);
 int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid, size_t *smem);
+int grid_for_smem(const ldu_matrix *A, const void *kernel, int block, size_t smem, int *grid);
 int meta_smem_bytes(int64_t n_slices, int num_sms, size_t *bytes);
 
 // ---------------------------------------------------------------------------
@@ -409,6 +414,19 @@ __device__ __forceinline__ void st_rows(float *p, const float (&o)[R]) {
 }
 
 template <int R>
+__device__ __forceinline__ void ld_rows(const int *p, int (&o)[R]) {
+    if constexpr (R == 4) {
+        int4 t = *reinterpret_cast<const int4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (R == 2) {
+        int2 t = *reinterpret_cast<const int2 *>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else {
+        o[0] = *p;
+    }
+}
+
+template <int R>
 __device__ __forceinline__ void ld_rows(const double *p, double (&o)[R]) {
     if constexpr (R >= 2) {
 #pragma unroll
@@ -561,10 +579,68 @@ __device__ __forceinline__ SliceRange block_slices(int n_slices) {
     return r;
 }
 
+// ---- bulk-copy staging of matrix slices (copy engine + mbarrier) -----------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// An L2 policy that marks lines evict-first: the matrix is read once per
+// sweep and must not push the (re-used) vectors out of L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// bytes from global src to shared dst, completing on bar (both 16-byte
+// aligned, bytes a multiple of 16), with L2 policy pol
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,
+                                              uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// order this thread's generic-proxy shared-memory accesses before later
+// async-proxy (bulk copy) writes to the same buffer
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Dynamic shared memory of the persistent kernels: (first slot, width) of
 // each slice the block owns, loaded once per launch, so the sweeps do not
 // wait on a global load before every slice's matrix loads.
-extern __shared__ int2 ldu_slice_meta[];
+extern __shared__ __align__(128) int2 ldu_slice_meta[];
 
 __device__ __forceinline__ void load_slice_meta(const SellView &A, const SliceRange &range) {
     if (A.meta_smem) {
@@ -578,6 +654,113 @@ __device__ __forceinline__ int2 slice_meta(const SellView &A, int s, const Slice
     if (A.meta_smem)
         return ldu_slice_meta[s - range.begin];
     return make_int2(A.slice_ptr[s], A.slice_w[s]);
+}
+
+}  // namespace ldu
+
+namespace ldu {
+
+// ---- per-warp two-stage pipeline of matrix slices in shared memory --------
+// Dynamic shared memory: [slice metadata, meta_cap int2, padded to 128 B]
+// [stages: nwarps x 2 x stage_bytes][mbarriers: nwarps x 2].  A stage holds
+// a slice's int32 columns followed by its float values (stage_w x C each).
+// While a warp works on one slice from shared memory, the copy engine
+// brings the warp's next slice, so the DRAM latency of the matrix stream
+// leaves the dependency chain; only the (mostly L2-resident) gathers remain.
+struct SlicePipe {
+    char *buf;
+    uint64_t *bar;
+    unsigned stage_bytes;
+    unsigned val_off;
+    unsigned phase;   // bit k: parity the next wait on stage k expects
+};
+
+__host__ __device__ __forceinline__ size_t stage_area_offset(int meta_cap) {
+    return ((size_t)meta_cap * sizeof(int2) + 127) & ~(size_t)127;
+}
+
+__host__ __device__ __forceinline__ size_t staged_smem_bytes(int meta_cap, int nwarps, int stage_w,
+                                                             int C) {
+    return stage_area_offset(meta_cap) + (size_t)nwarps * 2 * stage_w * C * 8 +
+           (size_t)nwarps * 2 * sizeof(uint64_t);
+}
+
+__device__ __forceinline__ SlicePipe pipe_open(const SellView &A, int warp, int nwarps, int lane) {
+    char *base = reinterpret_cast<char *>(ldu_slice_meta) + stage_area_offset(A.meta_cap);
+    SlicePipe pp;
+    pp.stage_bytes = (unsigned)A.stage_w * A.C * 8u;
+    pp.val_off = (unsigned)A.stage_w * A.C * 4u;
+    pp.buf = base + (size_t)warp * 2 * pp.stage_bytes;
+    pp.bar = reinterpret_cast<uint64_t *>(base + (size_t)nwarps * 2 * pp.stage_bytes) + 2 * warp;
+    pp.phase = 0;
+    if (lane == 0) {
+        mbar_init(pp.bar, 1);
+        mbar_init(pp.bar + 1, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    return pp;
+}
+
+// lane 0 asks the copy engine for slice m into stage st
+__device__ __forceinline__ void pipe_issue(const SellView &A, SlicePipe &pp, int st, int2 m,
+                                           int lane) {
+    if (lane == 0) {
+        const unsigned bytes = (unsigned)m.y * A.C * 4u;
+        mbar_expect_tx(pp.bar + st, 2u * bytes);
+        if (bytes) {
+            char *dst = pp.buf + (size_t)st * pp.stage_bytes;
+            const uint64_t pol = l2_evict_first_policy();
+            bulk_copy_g2s(dst, A.col + m.x, bytes, pp.bar + st, pol);
+            bulk_copy_g2s(dst + pp.val_off, A.val32 + m.x, bytes, pp.bar + st, pol);
+        }
+    }
+}
+
+// every lane waits for stage st (bounded); the warp agrees on the outcome
+__device__ __forceinline__ bool pipe_wait(SlicePipe &pp, int st, unsigned long long timeout_ns) {
+    const unsigned par = (pp.phase >> st) & 1u;
+    pp.phase ^= (1u << st);
+    bool ok = mbar_try_wait(pp.bar + st, par);
+    if (!ok) {
+        const unsigned long long t0 = global_ns();
+        while (!(ok = mbar_try_wait(pp.bar + st, par)))
+            if (global_ns() - t0 > timeout_ns)
+                break;
+    }
+    return __all_sync(kFullMask, ok);
+}
+
+// acc[j] += sum_k val * x[col] for this lane's R rows, slots taken from a
+// staged slice in shared memory (same order of operations as sell_accum)
+template <int R>
+__device__ __forceinline__ void sell_accum_staged(const char *stage, unsigned val_off, int w, int C,
+                                                  int lane, const float *__restrict__ x,
+                                                  float (&acc)[R]) {
+    const int *scol = reinterpret_cast<const int *>(stage);
+    const float *sval = reinterpret_cast<const float *>(stage + val_off);
+    constexpr int KS = R == 4 ? 3 : 6;   // gathers in flight per batch (no spills at 128 regs)
+    for (int k0 = 0; k0 < w; k0 += KS) {
+        float g[KS][R];
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+            if (k0 + k < w) {
+                int c[R];
+                ld_rows<R>(scol + (k0 + k) * C + R * lane, c);
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    g[k][j] = x[c[j]];
+            }
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+            if (k0 + k < w) {
+                float v[R];
+                ld_rows<R>(sval + (k0 + k) * C + R * lane, v);
+#pragma unroll
+                for (int j = 0; j < R; ++j)
+                    acc[j] = fmaf(v[j], g[k][j], acc[j]);
+            }
+    }
 }
 
 }  // namespace ldu

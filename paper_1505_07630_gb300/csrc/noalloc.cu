@@ -223,6 +223,8 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     P.A.isd = isd;
     P.A.dg = dg;
     P.A.meta_smem = smem > 0;
+    P.A.meta_cap = (int)(smem / sizeof(int2));
+    P.A.stage_w = 0;
     P.sync.count = bar_count;
     P.sync.err = bar_err;
     P.sync.timeout_ns = 10ull * 1000000000ull;

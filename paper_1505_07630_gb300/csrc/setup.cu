@@ -41,6 +41,8 @@ SellView view_of(const ldu_matrix *A) {
     v.isd = A->isd;
     v.dg = A->dg;
     v.meta_smem = 0;   // set by the launcher once the shared memory is sized
+    v.meta_cap = 0;
+    v.stage_w = 0;
     return v;
 }
 
@@ -68,6 +70,27 @@ int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid, size
     int g = per_sm * A->num_sms;
     g = std::min(g, A->max_grid);
     *grid = g;
+    return LDU_OK;
+}
+
+// Grid for a given dynamic shared-memory size (raising the kernel's limit
+// above the default 48 KB when needed).
+int grid_for_smem(const ldu_matrix *A, const void *kernel, int block, size_t smem, int *grid) {
+    cudaError_t e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    if (per_sm < 1)
+        return LDU_ERR_UNSUPPORTED;
+    if (A->blocks_per_sm > 0)
+        per_sm = std::min(per_sm, A->blocks_per_sm);
+    *grid = std::min(per_sm * A->num_sms, A->max_grid);
     return LDU_OK;
 }
 
@@ -165,15 +188,17 @@ int ldu_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *neigh
     *out = nullptr;
     if (n < 0 || nf < 0 || (n > 0 && !diag) || (nf > 0 && (!owner || !neighbour || !upper || !lower)))
         return LDU_ERR_BAD_ARG;
-    int C = 128, bt = 256, bps = 0;
+    int C = 128, bt = 256, bps = 0, stg = 0;
     if (opt) {
         if (opt->slice_rows)
             C = opt->slice_rows;
         if (opt->block_threads)
             bt = opt->block_threads;
         bps = opt->blocks_per_sm;
+        stg = opt->staging;
     }
-    if ((C != 32 && C != 64 && C != 128) || (bt != 128 && bt != 256) || bps < 0)
+    if ((C != 32 && C != 64 && C != 128) || (bt != 128 && bt != 256) || bps < 0 ||
+        (stg != 0 && stg != -1))
         return LDU_ERR_BAD_ARG;
     if (n >= (int64_t)1 << 31 || nf >= (int64_t)1 << 30)
         return LDU_ERR_UNSUPPORTED;
@@ -203,6 +228,7 @@ int ldu_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *neigh
     A->C = C;
     A->block_threads = bt;
     A->blocks_per_sm = bps;
+    A->staging = stg;
     A->n_slices = (n + C - 1) / C;
     A->n_pad = A->n_slices * C;
     A->max_grid = A->num_sms * 32;

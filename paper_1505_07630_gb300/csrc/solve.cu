@@ -41,23 +41,55 @@ namespace {
 
 enum Kind { kPcg = 0, kPipe = 1, kMixed = 2, kMixedDeflated = 3 };
 
+// Resident blocks per SM the mixed kernel is compiled for: 2 by default;
+// 3 or 4 (fewer registers, more warps) where that compiles without spills.
+int mixed_minb(int R, int blocks_per_sm) {
+    if (blocks_per_sm >= 4 && R == 1)
+        return 4;
+    if (blocks_per_sm >= 3 && R <= 2)
+        return 3;
+    return 2;
+}
+
 template <int R>
-const void *kernel_ptr(Kind k) {
+const void *kernel_ptr(Kind k, int minb, bool stg) {
     switch (k) {
     case kPcg: return (const void *)k_pcg64<R, Batch<R>::pcg>;
     case kPipe: return (const void *)k_pipe64<R, Batch<R>::pipe>;
-    case kMixed: return (const void *)k_mixed<R, Batch<R>::mixed, false>;
-    default: return (const void *)k_mixed<R, Batch<R>::mixed, true>;
+    case kMixedDeflated: return (const void *)k_mixed<R, Batch<R>::mixed, true, 2, false>;
+    default:
+        if (stg)
+            return (const void *)k_mixed<R, Batch<R>::mixed, false, 2, true>;
+        if constexpr (R <= 2) {
+            if (minb == 3)
+                return (const void *)k_mixed<R, MixedBatch<R, 3>::kb, false, 3, false>;
+        }
+        if constexpr (R == 1) {
+            if (minb == 4)
+                return (const void *)k_mixed<R, MixedBatch<R, 4>::kb, false, 4, false>;
+        }
+        return (const void *)k_mixed<R, Batch<R>::mixed, false, 2, false>;
     }
 }
 
-const void *pick_kernel(const ldu_matrix *A, Kind k) {
+const void *pick_kernel(const ldu_matrix *A, Kind k, bool stg) {
+    const int R = A->C / 32;
+    const int minb = mixed_minb(R, A->blocks_per_sm);
     switch (A->C) {
-    case 32: return kernel_ptr<1>(k);
-    case 64: return kernel_ptr<2>(k);
-    default: return kernel_ptr<4>(k);
+    case 32: return kernel_ptr<1>(k, minb, stg);
+    case 64: return kernel_ptr<2>(k, minb, stg);
+    default: return kernel_ptr<4>(k, minb, stg);
     }
 }
+
+// Default iterations between FP64 residual replacements of the mixed solve:
+// on the 128^3 lognormal case 12 keeps the FP64 method's iteration count
+// (755 against 752), 16 loses 12 % of it to a plateau near convergence.
+constexpr int kMixedPeriod = 12;
+
+// Largest dynamic shared memory a block may take and still leave room for
+// two resident blocks per SM.
+constexpr size_t kStagedSmemMax = 100 * 1024;
 
 int map_status(int dev) {
     switch (dev) {
@@ -80,10 +112,8 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     if (opt.rr_period < 0 || opt.tau < 0.0 || opt.barrier_timeout_s < 0.0 ||
         (opt.deflate != 0 && opt.deflate != 1))
         return LDU_ERR_BAD_ARG;
-    if (kind == kMixed && opt.rr_period == 0 && !o)
-        opt.rr_period = 16;
-    if (kind == kMixed && o && o->rr_period == 0 && o->tau == 0.0)
-        opt.rr_period = 16;
+    if (kind == kMixed && opt.rr_period == 0 && opt.tau == 0.0)
+        opt.rr_period = kMixedPeriod;
     A->last = ldu_solve_stats{};
     if (A->n == 0) {
         if (iters)
@@ -93,15 +123,30 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
         A->last.status = LDU_OK;
         return LDU_OK;
     }
-    const void *kern = pick_kernel(A, (kind == kMixed && opt.deflate) ? kMixedDeflated : kind);
+    const Kind kk = (kind == kMixed && opt.deflate) ? kMixedDeflated : kind;
+    size_t meta = 0;
+    meta_smem_bytes(A->n_slices, A->num_sms, &meta);
+    const int meta_cap = (int)(meta / sizeof(int2));
+    size_t smem = meta;
+    bool stg = kk == kMixed && A->staging == 0 && A->max_w > 0 &&
+               mixed_minb(A->C / 32, A->blocks_per_sm) == 2;
+    if (stg) {
+        const size_t b = staged_smem_bytes(meta_cap, A->block_threads / 32, A->max_w, A->C);
+        if (b <= kStagedSmemMax)
+            smem = b;
+        else
+            stg = false;
+    }
+    const void *kern = pick_kernel(A, kk, stg);
     int grid = 0;
-    size_t smem = 0;
-    int rc = grid_for(A, kern, A->block_threads, &grid, &smem);
+    int rc = grid_for_smem(A, kern, A->block_threads, smem, &grid);
     if (rc != LDU_OK)
         return rc;
     SolveParams P;
     P.A = view_of(A);
-    P.A.meta_smem = smem > 0;
+    P.A.meta_smem = meta > 0;
+    P.A.meta_cap = meta_cap;
+    P.A.stage_w = stg ? A->max_w : 0;
     P.sync.count = A->bar_count;
     P.sync.err = A->bar_err;
     const double tmo = opt.barrier_timeout_s > 0.0 ? opt.barrier_timeout_s : 10.0;

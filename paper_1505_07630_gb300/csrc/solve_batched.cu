@@ -535,12 +535,14 @@ int pcg_solve_batched_async(const ldu_matrix *Ac, const double *b, double *x, do
         (opt.deflate != 0 && opt.deflate != 1))
         return LDU_ERR_BAD_ARG;
     if (precision == LDU_MIXED && opt.rr_period == 0 && opt.tau == 0.0)
-        opt.rr_period = 16;
+        opt.rr_period = 12;   // as the single-system default
     cudaStream_t st = (cudaStream_t)stream;
     const void *kern = batch_kernel(A->C, precision, precision == LDU_MIXED && opt.deflate);
     SolveParams P;
     P.A = view_of(A);
     P.A.meta_smem = Bt->smem > 0;
+    P.A.meta_cap = (int)(Bt->smem / sizeof(int2));
+    P.A.stage_w = 0;
     P.sync.count = A->bar_count;
     P.sync.err = A->bar_err;
     const double tmo = opt.barrier_timeout_s > 0.0 ? opt.barrier_timeout_s : 10.0;

@@ -99,6 +99,15 @@ struct Batch {
     static constexpr int mixed = R == 4 ? 2 : (R == 2 ? 3 : 6);
 };
 
+// The mixed sweep is bound by chains of dependent loads, so more resident
+// warps help; these (rows per lane, blocks per SM) pairs compile without
+// spills at the register share that occupancy leaves (80 registers at 3
+// blocks, 64 at 4), with the batch given here.
+template <int R, int MINB>
+struct MixedBatch {
+    static constexpr int kb = MINB == 2 ? Batch<R>::mixed : (R == 1 && MINB == 3 ? 3 : 2);
+};
+
 // FP64 reduction of K partials: block sums -> slot -> barrier -> totals.
 // Returns false when the barrier failed (the kernel must return).
 template <int K>
@@ -671,7 +680,7 @@ struct MixedState {
     int it, since, reps, status, fresh, force;
 };
 
-template <int R, int KB, bool DEFL>
+template <int R, int KB, bool DEFL, bool STG = false>
 __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc) {
     __syncthreads();   // the previous body of this block is done with shared state
     LANE_ROWS;
@@ -682,6 +691,12 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
     float *z = P.v32[4], *sv = P.v32[5], *p = P.v32[6];
     float *w0f = P.v32[7], *q0f = P.v32[8], *t0f = P.v32[9];
     constexpr bool defl = DEFL;   // a separate instantiation keeps the plain loop lean
+    // per-warp slice pipeline: its mbarriers are set up once per solve and
+    // every sweep consumes exactly the copies it issues, so the phases stay
+    // in step from one sweep to the next
+    SlicePipe pipe;
+    if constexpr (STG)
+        pipe = pipe_open(A, warp, nwarps, lane);
     __shared__ MixedCtl ctl;
     const bool t0 = threadIdx.x == 0;
     unsigned epoch = 0;
@@ -1003,6 +1018,19 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
         const float *w = wc ? wb : wa;
         float *wn = wc ? wa : wb;
         KahanF g0, g1, g2;   // per-thread partial dots, compensated
+        // staged sweep: this warp's slices s_k = first + k * nwarps, the
+        // matrix of slice k + 2 in flight while slice k is computed
+        int first = 0, nk = 0;
+        bool staged_ok = true;
+        if constexpr (STG) {
+            first = range.begin + warp;
+            nk = first < range.end ? (range.end - first + nwarps - 1) / nwarps : 0;
+            if (nk > 0)
+                pipe_issue(A, pipe, 0, slice_meta(A, first, range), lane);
+            if (nk > 1)
+                pipe_issue(A, pipe, 1, slice_meta(A, first + nwarps, range), lane);
+        }
+        int kslice = 0;
         FOR_MY_SLICES(s) {
             const int row0 = s * A.C + R * lane;
             float nn[R], ww[R];
@@ -1010,7 +1038,22 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 nn[j] = ww[j];
-            sell_accum<float, R, KB>(A, slice_meta(A, s, range), lane, w, nn);
+            if constexpr (STG) {
+                const int st = kslice & 1;
+                if (!pipe_wait(pipe, st, P.sync.timeout_ns)) {
+                    staged_ok = false;
+                    break;
+                }
+                sell_accum_staged<R>(pipe.buf + (size_t)st * pipe.stage_bytes, pipe.val_off,
+                                     slice_meta(A, s, range).y, A.C, lane, w, nn);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (kslice + 2 < nk)
+                    pipe_issue(A, pipe, st, slice_meta(A, s + 2 * nwarps, range), lane);
+                ++kslice;
+            } else {
+                sell_accum<float, R, KB>(A, slice_meta(A, s, range), lane, w, nn);
+            }
             float zz[R], ss[R], pp[R], xx[R], rr[R];
             ld_rows<R>(z + row0, zz);
             ld_rows<R>(sv + row0, ss);
@@ -1058,6 +1101,16 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
             st_rows<R>(r + row0, rr);
             st_rows<R>(wn + row0, ww);
         }
+        if constexpr (STG) {
+            if (!staged_ok) {
+                // a copy never completed: record it, let copies still in
+                // flight land (bounded), and stop at the next barrier
+                if (lane == 0)
+                    atomicCAS(P.sync.err, 0, kDevTimeout);
+                pipe_wait(pipe, 0, P.sync.timeout_ns);
+                pipe_wait(pipe, 1, P.sync.timeout_ns);
+            }
+        }
         FF fp[3] = {g0.ff(), g1.ff(), g2.ff()};
         double tp[3];
         if (!reduce_f<3>(P, sc, fp, tp, epoch, parity))
@@ -1077,12 +1130,12 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
     return true;
 }
 
-template <int R, int KB, bool DEFL>
-__global__ void __launch_bounds__(256, 2) k_mixed(SolveParams P) {
+template <int R, int KB, bool DEFL, int MINB, bool STG>
+__global__ void __launch_bounds__(256, MINB) k_mixed(SolveParams P) {
     if (P.fault_inject && blockIdx.x == 0)
         return;   // test hook: this block never arrives at a barrier
     const Scope sc = grid_scope(P);
-    mixed_body<R, KB, DEFL>(P, sc);
+    mixed_body<R, KB, DEFL, STG>(P, sc);
 }
 
 }  // namespace
