@@ -82,9 +82,11 @@ def profiled_traffic():
 # Per cell, with f = 2F/n off-diagonal entries per row (actual, padding
 # excluded), float values/indices 4 B, double 8 B; vectors counted once per
 # pass they are read or written, gathers once.
-def bytes_mixed(n, F, iters, reps):
+def bytes_mixed(n, F, iters, reps, col_bytes=4):
+    """col_bytes: bytes per column index in the float loop (2 when the staged
+    sweep reads 16-bit column offsets)."""
     f = 2.0 * F / n
-    loop = f * 8 + 6 * 4 + 6 * 4                  # matrix (val32+col) + 6 reads + 6 writes
+    loop = f * (4 + col_bytes) + 6 * 4 + 6 * 4    # matrix (val32+col) + 6 reads + 6 writes
     rep = (24                                     # fold: xhat rw, xc rw
            + f * 12 + 8 + 8 + 8 + 8 + 4           # FP64 residual: val64+col, xhat, bhat, dg, r out
            + f * 8 + 4 + 4 + 4 + 4                # w = Ar, s = Ap
@@ -312,7 +314,8 @@ def run_ours(args):
     grid = A.stats()
     step_s = total / args.steps
     hbm, peak_kind = peaks()
-    alg_bytes = bytes_mixed(n, F, it, reps)
+    col_bytes = 2 if (A.info()["col16"] and grid["staged"]) else 4
+    alg_bytes = bytes_mixed(n, F, it, reps, col_bytes)
     achieved = alg_bytes / statistics.median(t_mixed) / 1e9
     prof = profiled_traffic()
     traffic = None
@@ -413,7 +416,9 @@ def run_ours(args):
                      "kernel": "k_mixed (persistent, one launch per solve)",
                      "alg_bytes_per_launch": alg_bytes},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n,
-                "d2h_bytes_per_step": 8 * n},
+                "d2h_bytes_per_step": 8 * n,
+                "step_ms_min_median_max": [min(t_e2e) * 1e3, statistics.median(t_e2e) * 1e3,
+                                           max(t_e2e) * 1e3]},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

@@ -109,6 +109,8 @@ typedef struct ldu_solve_stats {
     double bnorm;           /* ||b||_2 */
     int grid_blocks;        /* blocks of the persistent launch */
     int block_threads;
+    int staged;             /* 1 when the float sweeps staged the matrix in
+                               shared memory, 0 for plain loads */
 } ldu_solve_stats;
 
 /* Facts about a handle's device layout. */
@@ -120,6 +122,10 @@ typedef struct ldu_info {
     int64_t n_slices;
     int max_row_entries;    /* widest slice */
     int64_t device_bytes;   /* bytes the handle holds on the device */
+    int col16;              /* 1: the handle also stores each slot's column as a
+                               16-bit offset from its row (every offset fits),
+                               which the staged float sweeps read instead of
+                               the int32 columns */
 } ldu_info;
 
 /* Create a handle from an LDU matrix (Sec. 5, lduMatrix; Eq. 9's A).

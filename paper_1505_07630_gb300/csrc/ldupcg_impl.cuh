@@ -63,6 +63,8 @@ struct SellView {
     const int *slice_ptr;   // [n_slices + 1], in slots
     const int *slice_w;     // [n_slices]
     const int *col;         // [nnz_pad]
+    const short *col16;     // [nnz_pad] column minus row of each slot when every slot
+                            // fits in 16 bits (null otherwise); read by staged sweeps
     const double *val64;    // [nnz_pad]
     const float *val32;     // [nnz_pad]
     const double *sd;       // [n_pad]
@@ -72,6 +74,7 @@ struct SellView {
     int meta_cap;           // slice entries reserved for that metadata in shared memory
     int stage_w;            // > 0: float sweeps stage (col, val32) slices of width <= stage_w
                             // into shared memory with bulk copies; 0: plain global loads
+    int stages;             // pipeline depth per warp when staging (2..kMaxStages)
 };
 
 // Barrier state shared by the blocks of one persistent launch.
@@ -99,6 +102,7 @@ struct ldu_matrix {
     int64_t device_bytes;
     // structure
     int *slice_ptr, *slice_w, *col;
+    short *col16;              // 16-bit column offsets (null when some offset does not fit)
     uint32_t *fid;
     int32_t *owner, *neighbour;
     // values
@@ -427,6 +431,19 @@ __device__ __forceinline__ void ld_rows(const int *p, int (&o)[R]) {
 }
 
 template <int R>
+__device__ __forceinline__ void ld_rows(const short *p, int (&o)[R]) {
+    if constexpr (R == 4) {
+        short4 t = *reinterpret_cast<const short4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (R == 2) {
+        short2 t = *reinterpret_cast<const short2 *>(p);
+        o[0] = t.x; o[1] = t.y;
+    } else {
+        o[0] = *p;
+    }
+}
+
+template <int R>
 __device__ __forceinline__ void ld_rows(const double *p, double (&o)[R]) {
     if constexpr (R >= 2) {
 #pragma unroll
@@ -566,6 +583,40 @@ __device__ __forceinline__ void sell_accum2(const SellView &A, int2 m, int lane,
     }
 }
 
+// acc64 += Ahat64 x64 (double values) and acc32 += Ahat32 x32 (float values)
+// through the same slots: one read of the columns serves an FP64 and a float
+// product, each accumulated in slot order as sell_accum does.
+template <int R, int KB>
+__device__ __forceinline__ void sell_accum_df(const SellView &A, int2 m, int lane,
+                                              const double *__restrict__ x64,
+                                              const float *__restrict__ x32, double (&acc64)[R],
+                                              float (&acc32)[R]) {
+    const int w = m.y;
+    const int C = A.C;
+    const int base = m.x + R * lane;
+    for (int k0 = 0; k0 < w; k0 += KB) {
+        int c[KB][R];
+        double v[KB][R];
+        float u[KB][R];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+            if (k0 + k < w) {
+                ld_stream<R>(A.col + base + (k0 + k) * C, c[k]);
+                ld_stream<R>(A.val64 + base + (k0 + k) * C, v[k]);
+                ld_stream<R>(A.val32 + base + (k0 + k) * C, u[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KB; ++k)
+#pragma unroll
+            for (int j = 0; j < R; ++j)
+                if (k0 + k < w) {
+                    acc64[j] = fma(v[k][j], x64[c[k][j]], acc64[j]);
+                    acc32[j] = fmaf(u[k][j], x32[c[k][j]], acc32[j]);
+                }
+    }
+}
+
 // Slices of the calling block: a contiguous range, warps interleaved in it.
 struct SliceRange {
     int begin, end;
@@ -660,67 +711,89 @@ __device__ __forceinline__ int2 slice_meta(const SellView &A, int s, const Slice
 
 namespace ldu {
 
-// ---- per-warp two-stage pipeline of matrix slices in shared memory --------
+// ---- per-warp pipeline of matrix slices in shared memory -----------------
 // Dynamic shared memory: [slice metadata, meta_cap int2, padded to 128 B]
-// [stages: nwarps x 2 x stage_bytes][mbarriers: nwarps x 2].  A stage holds
-// a slice's int32 columns followed by its float values (stage_w x C each).
-// While a warp works on one slice from shared memory, the copy engine
-// brings the warp's next slice, so the DRAM latency of the matrix stream
-// leaves the dependency chain; only the (mostly L2-resident) gathers remain.
+// [stages: nwarps x nst x stage_bytes][mbarriers: nwarps x nst].  A stage
+// holds a slice's columns (16-bit offsets, else int32) followed by its float
+// values (stage_w x C each).  While a warp works on one slice from shared
+// memory, the copy engine brings its next nst - 1 slices, so the DRAM
+// latency of the matrix stream leaves the dependency chain; only the
+// (mostly L2-resident) gathers remain.  Each sweep consumes exactly the
+// copies it issues, so the mbarrier phases stay in step across sweeps.
+constexpr int kMaxStages = 2;
+
 struct SlicePipe {
     char *buf;
     uint64_t *bar;
     unsigned stage_bytes;
     unsigned val_off;
     unsigned phase;   // bit k: parity the next wait on stage k expects
+    int nst;          // stages per warp
+    // the sweep in progress: this warp's k-th slice is first + k * nwarps
+    int first, nk, k, cur;
 };
 
 __host__ __device__ __forceinline__ size_t stage_area_offset(int meta_cap) {
     return ((size_t)meta_cap * sizeof(int2) + 127) & ~(size_t)127;
 }
 
+// bytes of one stage: col_bytes per column (2 or 4) plus a float per slot
+__host__ __device__ __forceinline__ size_t stage_bytes(int stage_w, int C, int col_bytes) {
+    return (size_t)stage_w * C * (size_t)(col_bytes + 4);
+}
+
 __host__ __device__ __forceinline__ size_t staged_smem_bytes(int meta_cap, int nwarps, int stage_w,
-                                                             int C) {
-    return stage_area_offset(meta_cap) + (size_t)nwarps * 2 * stage_w * C * 8 +
-           (size_t)nwarps * 2 * sizeof(uint64_t);
+                                                             int C, int col_bytes, int nst) {
+    return stage_area_offset(meta_cap) + (size_t)nwarps * nst * stage_bytes(stage_w, C, col_bytes) +
+           (size_t)nwarps * nst * sizeof(uint64_t);
 }
 
 __device__ __forceinline__ SlicePipe pipe_open(const SellView &A, int warp, int nwarps, int lane) {
     char *base = reinterpret_cast<char *>(ldu_slice_meta) + stage_area_offset(A.meta_cap);
+    const int cb = A.col16 ? 2 : 4;
     SlicePipe pp;
-    pp.stage_bytes = (unsigned)A.stage_w * A.C * 8u;
-    pp.val_off = (unsigned)A.stage_w * A.C * 4u;
-    pp.buf = base + (size_t)warp * 2 * pp.stage_bytes;
-    pp.bar = reinterpret_cast<uint64_t *>(base + (size_t)nwarps * 2 * pp.stage_bytes) + 2 * warp;
+    pp.nst = A.stages;
+    pp.stage_bytes = (unsigned)stage_bytes(A.stage_w, A.C, cb);
+    pp.val_off = (unsigned)A.stage_w * A.C * (unsigned)cb;
+    pp.buf = base + (size_t)warp * pp.nst * pp.stage_bytes;
+    pp.bar = reinterpret_cast<uint64_t *>(base + (size_t)nwarps * pp.nst * pp.stage_bytes) +
+             pp.nst * warp;
     pp.phase = 0;
+    pp.first = pp.nk = pp.k = pp.cur = 0;
     if (lane == 0) {
-        mbar_init(pp.bar, 1);
-        mbar_init(pp.bar + 1, 1);
+        for (int j = 0; j < pp.nst; ++j)
+            mbar_init(pp.bar + j, 1);
         mbar_init_fence();
     }
     __syncwarp();
     return pp;
 }
 
-// lane 0 asks the copy engine for slice m into stage st
+// lane 0 asks the copy engine for slice m into stage st: its columns (16-bit
+// offsets when the handle has them, else int32) and its float values.  Slot
+// offsets are multiples of C >= 32, so every source address, destination
+// offset and size is a multiple of 64 bytes.
 __device__ __forceinline__ void pipe_issue(const SellView &A, SlicePipe &pp, int st, int2 m,
                                            int lane) {
     if (lane == 0) {
-        const unsigned bytes = (unsigned)m.y * A.C * 4u;
-        mbar_expect_tx(pp.bar + st, 2u * bytes);
-        if (bytes) {
+        const unsigned vbytes = (unsigned)m.y * A.C * 4u;
+        const unsigned cbytes = A.col16 ? vbytes / 2u : vbytes;
+        mbar_expect_tx(pp.bar + st, cbytes + vbytes);
+        if (vbytes) {
             char *dst = pp.buf + (size_t)st * pp.stage_bytes;
             const uint64_t pol = l2_evict_first_policy();
-            bulk_copy_g2s(dst, A.col + m.x, bytes, pp.bar + st, pol);
-            bulk_copy_g2s(dst + pp.val_off, A.val32 + m.x, bytes, pp.bar + st, pol);
+            const void *csrc = A.col16 ? (const void *)(A.col16 + m.x) : (const void *)(A.col + m.x);
+            bulk_copy_g2s(dst, csrc, cbytes, pp.bar + st, pol);
+            bulk_copy_g2s(dst + pp.val_off, A.val32 + m.x, vbytes, pp.bar + st, pol);
         }
     }
 }
 
-// every lane waits for stage st (bounded); the warp agrees on the outcome
+// every lane waits for stage st (bounded); the warp agrees on the outcome.
+// The expected parity advances only on success, so that a drain after a
+// timeout waits for the same phase again.
 __device__ __forceinline__ bool pipe_wait(SlicePipe &pp, int st, unsigned long long timeout_ns) {
     const unsigned par = (pp.phase >> st) & 1u;
-    pp.phase ^= (1u << st);
     bool ok = mbar_try_wait(pp.bar + st, par);
     if (!ok) {
         const unsigned long long t0 = global_ns();
@@ -728,18 +801,67 @@ __device__ __forceinline__ bool pipe_wait(SlicePipe &pp, int st, unsigned long l
             if (global_ns() - t0 > timeout_ns)
                 break;
     }
-    return __all_sync(kFullMask, ok);
+    ok = __all_sync(kFullMask, ok);
+    if (ok)
+        pp.phase ^= (1u << st);
+    return ok;
+}
+
+// start a sweep over this warp's slices of range: fill the pipeline
+__device__ __forceinline__ void pipe_begin(const SellView &A, SlicePipe &pp,
+                                          const SliceRange &range, int warp, int nwarps,
+                                          int lane) {
+    pp.first = range.begin + warp;
+    pp.nk = pp.first < range.end ? (range.end - pp.first + nwarps - 1) / nwarps : 0;
+    pp.k = 0;
+    pp.cur = 0;
+    const int fill = pp.nk < pp.nst ? pp.nk : pp.nst;
+    for (int j = 0; j < fill; ++j)
+        pipe_issue(A, pp, j, slice_meta(A, pp.first + j * nwarps, range), lane);
+}
+
+// wait for the warp's current slice; returns its stage, or null on timeout
+__device__ __forceinline__ const char *pipe_front(SlicePipe &pp, unsigned long long timeout_ns) {
+    if (!pipe_wait(pp, pp.cur, timeout_ns))
+        return nullptr;
+    return pp.buf + (size_t)pp.cur * pp.stage_bytes;
+}
+
+// the current stage has been read: order those reads before the copy
+// engine's next write into it, refill it with slice k + nst, advance
+__device__ __forceinline__ void pipe_pop(const SellView &A, SlicePipe &pp, const SliceRange &range,
+                                        int nwarps, int lane) {
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (pp.k + pp.nst < pp.nk)
+        pipe_issue(A, pp, pp.cur, slice_meta(A, pp.first + (pp.k + pp.nst) * nwarps, range),
+                   lane);
+    ++pp.k;
+    pp.cur = pp.cur + 1 == pp.nst ? 0 : pp.cur + 1;
+}
+
+// after a timeout: wait (bounded) for every copy still in flight, so that
+// none lands in shared memory after the block has left
+__device__ __forceinline__ void pipe_drain(SlicePipe &pp, unsigned long long timeout_ns) {
+    const int left = pp.nk - pp.k;
+    const int n = left < pp.nst ? left : pp.nst;
+    int st = pp.cur;
+    for (int j = 0; j < n; ++j) {
+        pipe_wait(pp, st, timeout_ns);
+        st = st + 1 == pp.nst ? 0 : st + 1;
+    }
 }
 
 // acc[j] += sum_k val * x[col] for this lane's R rows, slots taken from a
-// staged slice in shared memory (same order of operations as sell_accum)
-template <int R>
+// staged slice in shared memory (same order of operations as sell_accum);
+// KS slots' gathers are in flight per batch.  CT = short: the stage holds
+// column minus row, and row0 is the lane's first row.
+template <int R, int KS, typename CT>
 __device__ __forceinline__ void sell_accum_staged(const char *stage, unsigned val_off, int w, int C,
-                                                  int lane, const float *__restrict__ x,
+                                                  int lane, int row0, const float *__restrict__ x,
                                                   float (&acc)[R]) {
-    const int *scol = reinterpret_cast<const int *>(stage);
+    const CT *scol = reinterpret_cast<const CT *>(stage);
     const float *sval = reinterpret_cast<const float *>(stage + val_off);
-    constexpr int KS = R == 4 ? 3 : 6;   // gathers in flight per batch (no spills at 128 regs)
     for (int k0 = 0; k0 < w; k0 += KS) {
         float g[KS][R];
 #pragma unroll
@@ -748,8 +870,11 @@ __device__ __forceinline__ void sell_accum_staged(const char *stage, unsigned va
                 int c[R];
                 ld_rows<R>(scol + (k0 + k) * C + R * lane, c);
 #pragma unroll
-                for (int j = 0; j < R; ++j)
+                for (int j = 0; j < R; ++j) {
+                    if constexpr (sizeof(CT) == 2)
+                        c[j] += row0 + j;
                     g[k][j] = x[c[j]];
+                }
             }
 #pragma unroll
         for (int k = 0; k < KS; ++k)
@@ -759,6 +884,45 @@ __device__ __forceinline__ void sell_accum_staged(const char *stage, unsigned va
 #pragma unroll
                 for (int j = 0; j < R; ++j)
                     acc[j] = fmaf(v[j], g[k][j], acc[j]);
+            }
+    }
+}
+
+// Same for two vectors through the same staged slots (acc1 += Ahat x1,
+// acc2 += Ahat x2), in slot order.
+template <int R, int KS, typename CT>
+__device__ __forceinline__ void sell_accum2_staged(const char *stage, unsigned val_off, int w, int C,
+                                                   int lane, int row0,
+                                                   const float *__restrict__ x1,
+                                                   const float *__restrict__ x2, float (&acc1)[R],
+                                                   float (&acc2)[R]) {
+    const CT *scol = reinterpret_cast<const CT *>(stage);
+    const float *sval = reinterpret_cast<const float *>(stage + val_off);
+    for (int k0 = 0; k0 < w; k0 += KS) {
+        float g1[KS][R], g2[KS][R];
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+            if (k0 + k < w) {
+                int c[R];
+                ld_rows<R>(scol + (k0 + k) * C + R * lane, c);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    if constexpr (sizeof(CT) == 2)
+                        c[j] += row0 + j;
+                    g1[k][j] = x1[c[j]];
+                    g2[k][j] = x2[c[j]];
+                }
+            }
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+            if (k0 + k < w) {
+                float v[R];
+                ld_rows<R>(sval + (k0 + k) * C + R * lane, v);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    acc1[j] = fmaf(v[j], g1[k][j], acc1[j]);
+                    acc2[j] = fmaf(v[j], g2[k][j], acc2[j]);
+                }
             }
     }
 }

@@ -217,6 +217,7 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     P.A.slice_ptr = slice_ptr;
     P.A.slice_w = slice_w;
     P.A.col = col;
+    P.A.col16 = nullptr;
     P.A.val64 = val64;
     P.A.val32 = val32;
     P.A.sd = sd;
@@ -225,6 +226,7 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     P.A.meta_smem = smem > 0;
     P.A.meta_cap = (int)(smem / sizeof(int2));
     P.A.stage_w = 0;
+    P.A.stages = 0;
     P.sync.count = bar_count;
     P.sync.err = bar_err;
     P.sync.timeout_ns = 10ull * 1000000000ull;

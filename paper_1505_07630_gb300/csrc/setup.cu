@@ -35,6 +35,7 @@ SellView view_of(const ldu_matrix *A) {
     v.slice_ptr = A->slice_ptr;
     v.slice_w = A->slice_w;
     v.col = A->col;
+    v.col16 = A->col16;
     v.val64 = A->val64;
     v.val32 = A->val32;
     v.sd = A->sd;
@@ -43,6 +44,7 @@ SellView view_of(const ldu_matrix *A) {
     v.meta_smem = 0;   // set by the launcher once the shared memory is sized
     v.meta_cap = 0;
     v.stage_w = 0;
+    v.stages = 0;
     return v;
 }
 
@@ -133,7 +135,7 @@ void free_handle(ldu_matrix *A) {
     if (!A)
         return;
     ldu::free_batch(A);
-    void *ptrs[] = {A->slice_ptr, A->slice_w, A->col, A->fid, A->owner, A->neighbour,
+    void *ptrs[] = {A->slice_ptr, A->slice_w, A->col, A->col16, A->fid, A->owner, A->neighbour,
                     A->val64, A->sd, A->isd, A->dg, A->val32, A->slots, A->bar_count,
                     A->bar_err, A->out_dev, A->flags_dev, A->row_cell};
     for (void *p : ptrs)
@@ -310,6 +312,22 @@ int ldu_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *neigh
     if (n > 0)
         k_sort_rows<<<blocks_for(n, 128), 128, 0, st>>>((int)n, C, A->slice_ptr, deg, A->col, A->fid);
     CK(cudaGetLastError());
+    if (stg == 0 && A->nnz_pad > 0) {
+        // 16-bit column offsets for the staged sweeps, kept only if all fit
+        CK(dev_alloc(&A->col16, A->nnz_pad, &b));
+        k_col16<<<blocks_for(A->n_pad, 256), 256, 0, st>>>((int)A->n_pad, C, A->slice_ptr,
+                                                            A->slice_w, A->col, A->col16,
+                                                            A->flags_dev + 3);
+        CK(cudaGetLastError());
+        int overflow = 0;
+        CK(cudaMemcpyAsync(&overflow, A->flags_dev + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (overflow) {
+            cudaFree(A->col16);
+            A->col16 = nullptr;
+            b -= (int64_t)sizeof(short) * A->nnz_pad;
+        }
+    }
     if (A->n_pad > 0) {
         rc = values_from_arrays(A, diag, upper, lower, st);
         if (rc != LDU_OK)
@@ -452,6 +470,7 @@ int ldu_get_info(const ldu_matrix *A, ldu_info *info) {
     info->n_slices = A->n_slices;
     info->max_row_entries = A->max_w;
     info->device_bytes = A->device_bytes;
+    info->col16 = A->col16 ? 1 : 0;
     return LDU_OK;
 }
 

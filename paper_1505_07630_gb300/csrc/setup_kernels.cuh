@@ -118,6 +118,27 @@ __global__ void k_sort_rows(int n, int C, const int *slice_ptr, const int *deg, 
     }
 }
 
+// 16-bit offsets (column minus row) of every stored slot of row r; raises
+// kFlagOverflow when one does not fit, and the handle then keeps int32
+// columns only.
+__global__ void k_col16(int n_pad, int C, const int *slice_ptr, const int *slice_w, const int *col,
+                        short *col16, int *flag) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad)
+        return;
+    const int s = r / C, i = r - s * C;
+    const int base = slice_ptr[s] + i, w = slice_w[s];
+    bool fits = true;
+    for (int k = 0; k < w; ++k) {
+        const int d = col[base + k * C] - r;
+        const bool ok = d >= -32768 && d <= 32767;
+        fits = fits && ok;
+        col16[base + k * C] = ok ? (short)d : (short)0;
+    }
+    if (!fits)
+        atomicOr(flag, kFlagOverflow);
+}
+
 // diagonal scaling factors; padded rows get sd = isd = 1, dg = 0.  With a
 // row map (batched handles) diag is in the caller's cell order and rows
 // between systems (map -1) keep a unit diagonal.

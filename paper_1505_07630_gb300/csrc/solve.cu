@@ -56,10 +56,22 @@ const void *kernel_ptr(Kind k, int minb, bool stg) {
     switch (k) {
     case kPcg: return (const void *)k_pcg64<R, Batch<R>::pcg>;
     case kPipe: return (const void *)k_pipe64<R, Batch<R>::pipe>;
-    case kMixedDeflated: return (const void *)k_mixed<R, Batch<R>::mixed, true, 2, false>;
-    default:
+    case kMixedDeflated:
         if (stg)
+            return (const void *)k_mixed<R, Batch<R>::mixed, true, 2, true>;
+        return (const void *)k_mixed<R, Batch<R>::mixed, true, 2, false>;
+    default:
+        if (stg) {
+            if constexpr (R <= 2) {
+                if (minb == 3)
+                    return (const void *)k_mixed<R, MixedBatch<R, 3>::kb, false, 3, true>;
+            }
+            if constexpr (R == 1) {
+                if (minb == 4)
+                    return (const void *)k_mixed<R, MixedBatch<R, 4>::kb, false, 4, true>;
+            }
             return (const void *)k_mixed<R, Batch<R>::mixed, false, 2, true>;
+        }
         if constexpr (R <= 2) {
             if (minb == 3)
                 return (const void *)k_mixed<R, MixedBatch<R, 3>::kb, false, 3, false>;
@@ -87,9 +99,12 @@ const void *pick_kernel(const ldu_matrix *A, Kind k, bool stg) {
 // (755 against 752), 16 loses 12 % of it to a plateau near convergence.
 constexpr int kMixedPeriod = 12;
 
-// Largest dynamic shared memory a block may take and still leave room for
-// two resident blocks per SM.
-constexpr size_t kStagedSmemMax = 100 * 1024;
+// Largest dynamic shared memory a block of the staged mixed kernel may take
+// and still leave room for minb resident blocks per SM (228 KB per SM, less
+// 1 KB reserved and the kernel's static shared memory per block).
+size_t staged_smem_max(int minb) {
+    return (size_t)228 * 1024 / (size_t)minb - 5 * 1024;
+}
 
 int map_status(int dev) {
     switch (dev) {
@@ -128,14 +143,21 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     meta_smem_bytes(A->n_slices, A->num_sms, &meta);
     const int meta_cap = (int)(meta / sizeof(int2));
     size_t smem = meta;
-    bool stg = kk == kMixed && A->staging == 0 && A->max_w > 0 &&
-               mixed_minb(A->C / 32, A->blocks_per_sm) == 2;
+    const int minb = mixed_minb(A->C / 32, A->blocks_per_sm);
+    bool stg = (kk == kMixed || (kk == kMixedDeflated && minb == 2)) && A->staging == 0 &&
+               A->max_w > 0;
+    int nst = 0;
     if (stg) {
-        const size_t b = staged_smem_bytes(meta_cap, A->block_threads / 32, A->max_w, A->C);
-        if (b <= kStagedSmemMax)
-            smem = b;
-        else
-            stg = false;
+        // deepest pipeline that leaves room for minb blocks per SM
+        const int cb = A->col16 ? 2 : 4;
+        for (int d = kMaxStages; d >= 2 && nst == 0; --d) {
+            const size_t b = staged_smem_bytes(meta_cap, A->block_threads / 32, A->max_w, A->C, cb, d);
+            if (b <= staged_smem_max(minb)) {
+                smem = b;
+                nst = d;
+            }
+        }
+        stg = nst > 0;
     }
     const void *kern = pick_kernel(A, kk, stg);
     int grid = 0;
@@ -147,6 +169,7 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     P.A.meta_smem = meta > 0;
     P.A.meta_cap = meta_cap;
     P.A.stage_w = stg ? A->max_w : 0;
+    P.A.stages = nst;
     P.sync.count = A->bar_count;
     P.sync.err = A->bar_err;
     const double tmo = opt.barrier_timeout_s > 0.0 ? opt.barrier_timeout_s : 10.0;
@@ -202,6 +225,7 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     A->last.bnorm = out.bnorm;
     A->last.grid_blocks = grid;
     A->last.block_threads = A->block_threads;
+    A->last.staged = stg ? 1 : 0;
     if (status == LDU_OK || status == LDU_NOT_CONVERGED || status == LDU_ERR_NOT_SPD) {
         if (iters)
             *iters = out.iters;

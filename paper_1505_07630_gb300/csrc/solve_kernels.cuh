@@ -668,7 +668,7 @@ __global__ void __launch_bounds__(256, 2) k_pipe64(SolveParams P) {
 // w0 = D^1/2 1 / ||D^1/2 1||, with q0 = Ahat w0, t0 = Ahat q0 and
 // c = (w0, q0), all formed in FP64 at the start of the solve.
 struct MixedCtl {
-    double sigma;
+    double sigma, sigma_new;
     float a, bt, mu, f, pf;
     int action;   // 0 step, 1 replace, 2 exit
 };
@@ -680,7 +680,14 @@ struct MixedState {
     int it, since, reps, status, fresh, force;
 };
 
-template <int R, int KB, bool DEFL, bool STG = false>
+// Gathers in flight per batch in the staged sweep, spill-free at the
+// register budget of MINB resident blocks of 256 threads.
+template <int R, int MINB>
+struct StagedBatch {
+    static constexpr int ks = MINB == 2 ? (R == 4 ? 2 : 6) : (R == 1 ? (MINB == 4 ? 3 : 6) : 2);
+};
+
+template <int R, int KB, bool DEFL, bool STG = false, int SKS = 6>
 __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc) {
     __syncthreads();   // the previous body of this block is done with shared state
     LANE_ROWS;
@@ -691,9 +698,7 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
     float *z = P.v32[4], *sv = P.v32[5], *p = P.v32[6];
     float *w0f = P.v32[7], *q0f = P.v32[8], *t0f = P.v32[9];
     constexpr bool defl = DEFL;   // a separate instantiation keeps the plain loop lean
-    // per-warp slice pipeline: its mbarriers are set up once per solve and
-    // every sweep consumes exactly the copies it issues, so the phases stay
-    // in step from one sweep to the next
+    // per-warp slice pipeline: its mbarriers are set up once per solve
     SlicePipe pipe;
     if constexpr (STG)
         pipe = pipe_open(A, warp, nwarps, lane);
@@ -801,6 +806,21 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                                  (P.tau > 0.0 && S.gamma <= P.tau * P.tau * S.gamma_ref) ||
                                  S.ratio * S.gamma * S.sigma * S.sigma <= thr2 || S.it >= P.maxit;
             ctl.action = trigger ? 1 : 0;
+            if (trigger) {
+                // The float unit sigma of the next period, a power of two near
+                // the residual's norm, chosen before the true residual is
+                // formed (from the recursive residual, or ||b|| at the start)
+                // so that one pass can store r and s in the new unit.  Powers
+                // of two scale float arithmetic exactly, so the choice only
+                // keeps the float values in range.
+                const double est = S.gamma > 0.0 && S.gamma < 1e300 ? S.sigma * sqrt(S.gamma)
+                                                                     : sqrt(bn2);
+                const double sigma_new = exp2(rint(log2(est)));
+                const float f = (float)(S.sigma / sigma_new);
+                ctl.sigma_new = sigma_new;
+                ctl.f = f;
+                ctl.pf = P.restart ? 0.0f : f;
+            }
         }
         __syncthreads();
         if (ctl.action == 1) {
@@ -822,16 +842,20 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
             }
             if (!scope_sync(sc, P.sync, epoch))
                 return false;
-            // U2: FP64 true residual (deflated by the coarse correction), stored
-            // in float in units of the current sigma
-            const double inv_sigma = 1.0 / sig;   // power of two: exact
+            // U2: FP64 true residual (deflated by the coarse correction),
+            // stored in float in the new unit; in the same pass
+            // s = pf (Ahat p), which needs no scalar from this replacement
+            const double inv_sigma = 1.0 / ctl.sigma_new;   // power of two: exact
+            const float pf = ctl.pf;
             double part[2] = {0.0, 0.0}, tot[2];
             if (!defl) {
                 FOR_MY_SLICES(s) {
                     const int row0 = s * A.C + R * lane;
                     double acc[R], bb[R], dd[R];
+                    float as[R];
                     ld_rows<R>(xh + row0, acc);
-                    sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, xh, acc);
+                    ld_rows<R>(p + row0, as);
+                    sell_accum_df<R, KB>(A, slice_meta(A, s, range), lane, xh, p, acc, as);
                     ld_rows<R>(bh + row0, bb);
                     ld_rows<R>(A.dg + row0, dd);
                     float rf[R];
@@ -841,24 +865,30 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                         part[0] = fma(rj, rj, part[0]);
                         part[1] = fma(dd[j] * rj, rj, part[1]);
                         rf[j] = (float)(rj * inv_sigma);
+                        as[j] *= pf;
                     }
                     st_rows<R>(r + row0, rf);
+                    st_rows<R>(sv + row0, as);
                 }
             } else {
                 double pw[1] = {0.0}, tw[1];
                 FOR_MY_SLICES(s) {
                     const int row0 = s * A.C + R * lane;
                     double acc[R], bb[R], ww[R];
+                    float as[R];
                     ld_rows<R>(xh + row0, acc);
-                    sell_accum<double, R, KB>(A, slice_meta(A, s, range), lane, xh, acc);
+                    ld_rows<R>(p + row0, as);
+                    sell_accum_df<R, KB>(A, slice_meta(A, s, range), lane, xh, p, acc, as);
                     ld_rows<R>(bh + row0, bb);
                     ld_rows<R>(w0 + row0, ww);
 #pragma unroll
                     for (int j = 0; j < R; ++j) {
                         acc[j] = bb[j] - acc[j];
                         pw[0] = fma(ww[j], acc[j], pw[0]);
+                        as[j] *= pf;
                     }
                     st_rows<R>(rt + row0, acc);
+                    st_rows<R>(sv + row0, as);
                 }
                 if (!reduce_d<1>(P, sc, pw, tw, epoch, parity))
                     return false;
@@ -901,68 +931,76 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                     ctl.action = 2;
                 } else {
                     S.ratio = tot[1] / tot[0];
-                    const double sigma_new = exp2(rint(log2(sqrt(tot[0]))));
-                    const float f = (float)(S.sigma / sigma_new);
-                    ctl.f = f;
-                    ctl.pf = P.restart ? 0.0f : f;
                     if (P.restart)
                         S.fresh = 1;
                     else
-                        S.gamma_old *= (double)f * (double)f;
-                    S.sigma = sigma_new;
-                    ctl.sigma = sigma_new;
+                        S.gamma_old *= (double)ctl.f * (double)ctl.f;
+                    S.sigma = ctl.sigma_new;
+                    ctl.sigma = ctl.sigma_new;
                 }
             }
             __syncthreads();
             if (ctl.action == 2)
                 break;
-            const float f = ctl.f, pf = ctl.pf;
-            // U3: w = f (Ahat r) ; s = pf (Ahat p)
+            // U3: w = Ahat r ; z = Ahat s ; p *= pf ; gamma, delta (, eps).
+            // r and s are complete after the reduction's barrier and are only
+            // read here.
             float *w = wc ? wb : wa;
+            KahanF g0, g1, g2;
+            if constexpr (STG)
+                pipe_begin(A, pipe, range, warp, nwarps, lane);
+            bool staged_ok = true;
             FOR_MY_SLICES(s) {
                 const int row0 = s * A.C + R * lane;
-                float aw[R], as[R];
+                float aw[R], az[R], pp[R], qq[R];
                 ld_rows<R>(r + row0, aw);
-                ld_rows<R>(p + row0, as);
-                sell_accum2<float, R, KB>(A, slice_meta(A, s, range), lane, r, p, aw, as);
+                ld_rows<R>(sv + row0, az);
+                float rr[R];
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    aw[j] *= f;
-                    as[j] *= pf;
+                for (int j = 0; j < R; ++j)
+                    rr[j] = aw[j];
+                if constexpr (STG) {
+                    const char *stage = pipe_front(pipe, P.sync.timeout_ns);
+                    if (!stage) {
+                        staged_ok = false;
+                        break;
+                    }
+                    const int ws = slice_meta(A, s, range).y;
+                    if (A.col16)
+                        sell_accum2_staged<R, (SKS + 1) / 2, short>(stage, pipe.val_off, ws, A.C, lane, row0,
+                                                          r, sv, aw, az);
+                    else
+                        sell_accum2_staged<R, (SKS + 1) / 2, int>(stage, pipe.val_off, ws, A.C, lane, row0,
+                                                        r, sv, aw, az);
+                    pipe_pop(A, pipe, range, nwarps, lane);
+                } else {
+                    sell_accum2<float, R, KB>(A, slice_meta(A, s, range), lane, r, sv, aw, az);
                 }
                 st_rows<R>(w + row0, aw);
-                st_rows<R>(sv + row0, as);
-            }
-            if (!scope_sync(sc, P.sync, epoch))
-                return false;
-            // U4: z = Ahat s ; r *= f ; p *= pf ; gamma, delta (, eps)
-            KahanF g0, g1, g2;
-            FOR_MY_SLICES(s) {
-                const int row0 = s * A.C + R * lane;
-                float az[R], rr[R], pp[R], ww[R], qq[R];
-                ld_rows<R>(sv + row0, az);
-                sell_accum<float, R, KB>(A, slice_meta(A, s, range), lane, sv, az);
                 st_rows<R>(z + row0, az);
-                ld_rows<R>(r + row0, rr);
                 ld_rows<R>(p + row0, pp);
-                ld_rows<R>(w + row0, ww);
                 if (defl)
                     ld_rows<R>(q0f + row0, qq);
                 float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    rr[j] *= f;
                     pp[j] *= pf;
                     e0 = fmaf(rr[j], rr[j], e0);
-                    e1 = fmaf(ww[j], rr[j], e1);
+                    e1 = fmaf(aw[j], rr[j], e1);
                     if (defl)
                         e2 = fmaf(qq[j], rr[j], e2);
                 }
                 g0.add(e0);
                 g1.add(e1);
                 g2.add(e2);
-                st_rows<R>(r + row0, rr);
                 st_rows<R>(p + row0, pp);
+            }
+            if constexpr (STG) {
+                if (!staged_ok) {
+                    if (lane == 0)
+                        atomicCAS(P.sync.err, 0, kDevTimeout);
+                    pipe_drain(pipe, P.sync.timeout_ns);
+                }
             }
             FF fd[3] = {g0.ff(), g1.ff(), g2.ff()};
             double td[3];
@@ -1019,18 +1057,11 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
         float *wn = wc ? wa : wb;
         KahanF g0, g1, g2;   // per-thread partial dots, compensated
         // staged sweep: this warp's slices s_k = first + k * nwarps, the
-        // matrix of slice k + 2 in flight while slice k is computed
-        int first = 0, nk = 0;
+        // matrix of slices k + 1 .. k + nst - 1 in flight while slice k is
+        // computed
         bool staged_ok = true;
-        if constexpr (STG) {
-            first = range.begin + warp;
-            nk = first < range.end ? (range.end - first + nwarps - 1) / nwarps : 0;
-            if (nk > 0)
-                pipe_issue(A, pipe, 0, slice_meta(A, first, range), lane);
-            if (nk > 1)
-                pipe_issue(A, pipe, 1, slice_meta(A, first + nwarps, range), lane);
-        }
-        int kslice = 0;
+        if constexpr (STG)
+            pipe_begin(A, pipe, range, warp, nwarps, lane);
         FOR_MY_SLICES(s) {
             const int row0 = s * A.C + R * lane;
             float nn[R], ww[R];
@@ -1038,34 +1069,48 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 nn[j] = ww[j];
+            // the row vectors do not depend on the matrix: in the staged
+            // sweep their loads can go before the (memory-clobbering) wait
+            // so that their latency overlaps the gathers instead of
+            // following them; the plain sweep leaves the order to the
+            // compiler
+            float zz[R], ss[R], pp[R], xx[R], rr[R];
+            float dw[R], dq[R], dt[R];
+            auto load_rows = [&]() {
+                ld_rows<R>(z + row0, zz);
+                ld_rows<R>(sv + row0, ss);
+                ld_rows<R>(p + row0, pp);
+                ld_rows<R>(xc + row0, xx);
+                ld_rows<R>(r + row0, rr);
+                if (defl) {
+                    ld_rows<R>(w0f + row0, dw);
+                    ld_rows<R>(q0f + row0, dq);
+                    ld_rows<R>(t0f + row0, dt);
+                }
+            };
+            constexpr bool early = STG && R <= 2;   // 4 rows a lane: registers run short
+            if constexpr (early)
+                load_rows();
             if constexpr (STG) {
-                const int st = kslice & 1;
-                if (!pipe_wait(pipe, st, P.sync.timeout_ns)) {
+                const char *stage = pipe_front(pipe, P.sync.timeout_ns);
+                if (!stage) {
                     staged_ok = false;
                     break;
                 }
-                sell_accum_staged<R>(pipe.buf + (size_t)st * pipe.stage_bytes, pipe.val_off,
-                                     slice_meta(A, s, range).y, A.C, lane, w, nn);
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (kslice + 2 < nk)
-                    pipe_issue(A, pipe, st, slice_meta(A, s + 2 * nwarps, range), lane);
-                ++kslice;
+                const int ws = slice_meta(A, s, range).y;
+                if (A.col16)
+                    sell_accum_staged<R, SKS, short>(stage, pipe.val_off, ws, A.C, lane, row0, w,
+                                                     nn);
+                else
+                    sell_accum_staged<R, SKS, int>(stage, pipe.val_off, ws, A.C, lane, row0, w, nn);
+                pipe_pop(A, pipe, range, nwarps, lane);
             } else {
                 sell_accum<float, R, KB>(A, slice_meta(A, s, range), lane, w, nn);
             }
-            float zz[R], ss[R], pp[R], xx[R], rr[R];
-            ld_rows<R>(z + row0, zz);
-            ld_rows<R>(sv + row0, ss);
-            ld_rows<R>(p + row0, pp);
-            ld_rows<R>(xc + row0, xx);
-            ld_rows<R>(r + row0, rr);
+            if constexpr (!early)
+                load_rows();
             float e0 = 0.0f, e1 = 0.0f, e2 = 0.0f;
             if (defl) {
-                float dw[R], dq[R], dt[R];
-                ld_rows<R>(w0f + row0, dw);
-                ld_rows<R>(q0f + row0, dq);
-                ld_rows<R>(t0f + row0, dt);
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
                     zz[j] = fmaf(-mu, dt[j], fmaf(bt, zz[j], nn[j]));
@@ -1107,8 +1152,7 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                 // flight land (bounded), and stop at the next barrier
                 if (lane == 0)
                     atomicCAS(P.sync.err, 0, kDevTimeout);
-                pipe_wait(pipe, 0, P.sync.timeout_ns);
-                pipe_wait(pipe, 1, P.sync.timeout_ns);
+                pipe_drain(pipe, P.sync.timeout_ns);
             }
         }
         FF fp[3] = {g0.ff(), g1.ff(), g2.ff()};
@@ -1135,7 +1179,9 @@ __global__ void __launch_bounds__(256, MINB) k_mixed(SolveParams P) {
     if (P.fault_inject && blockIdx.x == 0)
         return;   // test hook: this block never arrives at a barrier
     const Scope sc = grid_scope(P);
-    mixed_body<R, KB, DEFL, STG>(P, sc);
+    // the deflated loop carries three more vectors: fewer gathers in flight
+    constexpr int ks = DEFL ? (StagedBatch<R, MINB>::ks + 1) / 2 : StagedBatch<R, MINB>::ks;
+    mixed_body<R, KB, DEFL, STG, ks>(P, sc);
 }
 
 }  // namespace

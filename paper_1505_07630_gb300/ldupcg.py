@@ -46,7 +46,7 @@ class LduSolveStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
                 ("replacements", ctypes.c_int), ("relres", ctypes.c_double),
                 ("bnorm", ctypes.c_double), ("grid_blocks", ctypes.c_int),
-                ("block_threads", ctypes.c_int)]
+                ("block_threads", ctypes.c_int), ("staged", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -56,7 +56,7 @@ class LduInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("n_padded", ctypes.c_int64),
                 ("nnz_padded", ctypes.c_int64), ("slice_rows", ctypes.c_int),
                 ("n_slices", ctypes.c_int64), ("max_row_entries", ctypes.c_int),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("col16", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -293,3 +293,61 @@ def test_set_face_coeffs_matches_assembly(pkg, oracle_mod):
     y2 = pkg.ldu_spmv(A, cuda(x)).cpu().numpy()
     assert np.all(np.abs(y2 - y_ref) <= 1e-13 * bound)
     A.close()
+
+
+@pytest.fixture(scope="module")
+def mixed_mid(oracle_mod):
+    """config 2 at 96^3 (884,736 cells): several slices per warp at every
+    slice height, so the staged pipeline refills its stages."""
+    s = lc.config2(s=96)
+    ref = oracle_mod.mixed_pipecg(s, tol=1e-8, period=12)
+    xs = oracle_mod.pcg(s, tol=1e-11).x
+    return s, ref, xs
+
+
+@pytest.mark.parametrize("staging", [0, -1])
+@pytest.mark.parametrize("C,bps", [(32, 0), (32, 3), (32, 4), (64, 0), (64, 3), (128, 0)])
+def test_mixed_launch_shapes(pkg, oracle_mod, mixed_mid, C, bps, staging):
+    """Every build of the mixed kernel (slice height x resident blocks per SM
+    x staged or plain matrix loads) against the oracle on the same case."""
+    s, ref, xs = mixed_mid
+    A = pkg.from_system(s, slice_rows=C, blocks_per_sm=bps, staging=staging)
+    x, st, it, rr = pkg.pipecg_solve(A, cuda(s.b), tol=1e-8, precision="mixed", rr_period=12)
+    stats = A.stats()
+    xh = x.cpu().numpy()
+    true_rr = oracle_mod.true_relres(s, xh)
+    assert st == 0 and true_rr <= 1.01e-8, (st, it, rr, true_rr)
+    assert abs(rr - true_rr) <= 1e-3 * true_rr
+    assert it <= 1.25 * ref.iters + 8, (it, ref.iters)
+    err = np.linalg.norm(xh - xs) / np.linalg.norm(xs)
+    err_ref = np.linalg.norm(ref.x - xs) / np.linalg.norm(xs)
+    assert err <= max(10 * err_ref, 1e-6)
+    if staging == -1:
+        assert stats["staged"] == 0
+    if bps:
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        assert stats["grid_blocks"] == bps * nsm
+    A.close()
+
+
+@pytest.mark.parametrize("ny,fits", [(32767, True), (32768, False), (20, True)])
+def test_col16_offsets_at_the_int16_limit(pkg, oracle_mod, ny, fits):
+    """A 1 x ny x 2 box numbers its z-neighbour ny rows away: 32767 is the
+    largest offset the 16-bit columns hold, 32768 sends the handle back to
+    int32 columns.  Both solve the same as the oracle (the diagonal is
+    scaled by 4, a strongly dominant diagonal, so a few iterations do)."""
+    s = lc.poisson_box(1, ny, 2, diffusivity="lognormal", seed=2)
+    s.diag = 4.0 * s.diag
+    A = pkg.from_system(s, slice_rows=64)
+    assert A.info()["col16"] == (1 if fits else 0)
+    ref = oracle_mod.mixed_pipecg(s, tol=1e-10, period=12)
+    x, st, it, rr = pkg.pipecg_solve(A, cuda(s.b), tol=1e-10, precision="mixed", rr_period=12)
+    assert A.stats()["staged"] == 1
+    xh = x.cpu().numpy()
+    assert st == 0 and oracle_mod.true_relres(s, xh) <= 1.01e-10
+    assert it <= 1.25 * ref.iters + 8
+    assert np.linalg.norm(xh - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    A.close()
+    B = pkg.from_system(s, slice_rows=64, staging=-1)
+    assert B.info()["col16"] == 0          # plain loads never read them
+    B.close()
