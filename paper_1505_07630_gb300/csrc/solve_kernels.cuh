@@ -684,7 +684,7 @@ struct MixedState {
 // register budget of MINB resident blocks of 256 threads.
 template <int R, int MINB>
 struct StagedBatch {
-    static constexpr int ks = MINB == 2 ? (R == 4 ? 2 : 6) : (R == 1 ? (MINB == 4 ? 3 : 6) : 2);
+    static constexpr int ks = MINB == 2 ? (R == 1 ? 6 : 1) : (R == 1 ? (MINB == 4 ? 3 : 6) : 2);
 };
 
 template <int R, int KB, bool DEFL, bool STG = false, int SKS = 6>
