@@ -161,9 +161,14 @@ __device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool team_sync(const GridSync &g, unsigned &epoch, unsigned members) {
+// lead = false: the caller has already passed a __syncthreads after its
+// threads' last global writes (a block reduction), so thread 0's release
+// covers them without another one.
+__device__ __forceinline__ bool team_sync(const GridSync &g, unsigned &epoch, unsigned members,
+                                          bool lead = true) {
     __shared__ int s_fail;
-    __syncthreads();
+    if (lead)
+        __syncthreads();
     epoch += 1;
     if (threadIdx.x == 0) {
         const unsigned target = epoch * members;
@@ -229,8 +234,16 @@ __device__ __forceinline__ void block_sum_to_slot(double (&v)[K], double *slot) 
 // order (thread t takes slots t, t + blockDim, ...; then a fixed tree), so
 // all blocks hold bitwise-identical totals.  All slot loads of a thread are
 // independent, so the sum costs about one L2 round trip.
-template <int K>
-__device__ __forceinline__ void grid_total(const double *slots, double (&out)[K], int members) {
+struct NoTail {
+    template <int K>
+    __device__ __forceinline__ void operator()(const double (&)[K]) const {}
+};
+
+// tail(totals) runs in thread 0 before the totals are published to the
+// block, so that the same barrier also publishes what it decides.
+template <int K, typename Tail = NoTail>
+__device__ __forceinline__ void grid_total(const double *slots, double (&out)[K], int members,
+                                           Tail tail = Tail()) {
     __shared__ double sm[32][K];
     __shared__ double res[K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -254,10 +267,12 @@ __device__ __forceinline__ void grid_total(const double *slots, double (&out)[K]
         for (int k = 0; k < K; ++k)
             t[k] = lane < nwarps ? sm[lane][k] : 0.0;
         warp_sum<K>(t);
-        if (lane == 0)
+        if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 res[k] = t[k];
+            tail(res);
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -348,8 +363,9 @@ __device__ __forceinline__ void block_sum_ff(FF (&v)[K], float2 *slot) {
 }
 
 // Float-pair grid total after a barrier (same fixed order in every block).
-template <int K>
-__device__ __forceinline__ void grid_total_ff(const float2 *slots, double (&out)[K], int members) {
+template <int K, typename Tail = NoTail>
+__device__ __forceinline__ void grid_total_ff(const float2 *slots, double (&out)[K], int members,
+                                              Tail tail = Tail()) {
     __shared__ FF sm[32][K];
     __shared__ double res[K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -375,10 +391,12 @@ __device__ __forceinline__ void grid_total_ff(const float2 *slots, double (&out)
         for (int k = 0; k < K; ++k)
             t[k] = lane < nwarps ? sm[lane][k] : FF{0.0f, 0.0f};
         warp_sum_ff<K>(t);
-        if (lane == 0)
+        if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 res[k] = ff_value(t[k]);
+            tail(res);
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -731,6 +749,7 @@ struct SlicePipe {
     int nst;          // stages per warp
     // the sweep in progress: this warp's k-th slice is first + k * nwarps
     int first, nk, k, cur;
+    bool primed;      // the next sweep's first slices are already in flight
 };
 
 __host__ __device__ __forceinline__ size_t stage_area_offset(int meta_cap) {
@@ -760,6 +779,7 @@ __device__ __forceinline__ SlicePipe pipe_open(const SellView &A, int warp, int 
              pp.nst * warp;
     pp.phase = 0;
     pp.first = pp.nk = pp.k = pp.cur = 0;
+    pp.primed = false;
     if (lane == 0) {
         for (int j = 0; j < pp.nst; ++j)
             mbar_init(pp.bar + j, 1);
@@ -807,10 +827,12 @@ __device__ __forceinline__ bool pipe_wait(SlicePipe &pp, int st, unsigned long l
     return ok;
 }
 
-// start a sweep over this warp's slices of range: fill the pipeline
-__device__ __forceinline__ void pipe_begin(const SellView &A, SlicePipe &pp,
-                                          const SliceRange &range, int warp, int nwarps,
-                                          int lane) {
+// fill the pipeline with the first slices of a sweep over this warp's
+// slices of range (every staged sweep visits the same slices in the same
+// order, and the matrix does not change during a solve)
+__device__ __forceinline__ void pipe_fill(const SellView &A, SlicePipe &pp,
+                                         const SliceRange &range, int warp, int nwarps,
+                                         int lane) {
     pp.first = range.begin + warp;
     pp.nk = pp.first < range.end ? (range.end - pp.first + nwarps - 1) / nwarps : 0;
     pp.k = 0;
@@ -818,6 +840,25 @@ __device__ __forceinline__ void pipe_begin(const SellView &A, SlicePipe &pp,
     const int fill = pp.nk < pp.nst ? pp.nk : pp.nst;
     for (int j = 0; j < fill; ++j)
         pipe_issue(A, pp, j, slice_meta(A, pp.first + j * nwarps, range), lane);
+}
+
+// start a sweep: fill the pipeline unless the end of the previous sweep did
+__device__ __forceinline__ void pipe_begin(const SellView &A, SlicePipe &pp,
+                                          const SliceRange &range, int warp, int nwarps,
+                                          int lane) {
+    if (!pp.primed)
+        pipe_fill(A, pp, range, warp, nwarps, lane);
+    pp.primed = false;
+}
+
+// end of a sweep whose slices have all been consumed: start the copies of
+// the next sweep's first slices, so that their latency overlaps the grid
+// reduction that follows
+__device__ __forceinline__ void pipe_prime(const SellView &A, SlicePipe &pp,
+                                          const SliceRange &range, int warp, int nwarps,
+                                          int lane) {
+    pipe_fill(A, pp, range, warp, nwarps, lane);
+    pp.primed = true;
 }
 
 // wait for the warp's current slice; returns its stage, or null on timeout
@@ -840,8 +881,8 @@ __device__ __forceinline__ void pipe_pop(const SellView &A, SlicePipe &pp, const
     pp.cur = pp.cur + 1 == pp.nst ? 0 : pp.cur + 1;
 }
 
-// after a timeout: wait (bounded) for every copy still in flight, so that
-// none lands in shared memory after the block has left
+// wait (bounded) for every copy still in flight, so that none lands in
+// shared memory after the block has left; the pipeline is empty afterwards
 __device__ __forceinline__ void pipe_drain(SlicePipe &pp, unsigned long long timeout_ns) {
     const int left = pp.nk - pp.k;
     const int n = left < pp.nst ? left : pp.nst;
@@ -850,7 +891,19 @@ __device__ __forceinline__ void pipe_drain(SlicePipe &pp, unsigned long long tim
         pipe_wait(pp, st, timeout_ns);
         st = st + 1 == pp.nst ? 0 : st + 1;
     }
+    pp.k = pp.nk;
+    pp.primed = false;
 }
+
+// Drains the pipeline when the solve body returns, on every path.
+struct PipeGuard {
+    SlicePipe *pp;
+    unsigned long long timeout_ns;
+    __device__ __forceinline__ ~PipeGuard() {
+        if (pp)
+            pipe_drain(*pp, timeout_ns);
+    }
+};
 
 // acc[j] += sum_k val * x[col] for this lane's R rows, slots taken from a
 // staged slice in shared memory (same order of operations as sell_accum);

@@ -64,14 +64,15 @@ __device__ __forceinline__ const double *slots_all(const Scope &sc, int parity) 
 }
 
 // Barrier over the scope's blocks; a one-block scope needs only __syncthreads.
-__device__ __forceinline__ bool scope_sync(const Scope &sc, const GridSync &g, unsigned &epoch) {
+__device__ __forceinline__ bool scope_sync(const Scope &sc, const GridSync &g, unsigned &epoch,
+                                           bool lead = true) {
     if (sc.members == 1) {
         __syncthreads();
         return true;
     }
     GridSync t = g;
     t.count = sc.count;
-    return team_sync(t, epoch, (unsigned)sc.members);
+    return team_sync(t, epoch, (unsigned)sc.members, lead);
 }
 
 // The whole grid as one scope (single-system launch).
@@ -110,25 +111,31 @@ struct MixedBatch {
 
 // FP64 reduction of K partials: block sums -> slot -> barrier -> totals.
 // Returns false when the barrier failed (the kernel must return).
-template <int K>
+// tail(totals) runs in thread 0 before the totals reach the block (see
+// grid_total).  The block sum ends with a __syncthreads after every thread's
+// writes, so the barrier needs no leading one.
+template <int K, typename Tail = NoTail>
 __device__ __forceinline__ bool reduce_d(const SolveParams &P, const Scope &sc, double (&part)[K],
-                                         double (&tot)[K], unsigned &epoch, int &parity) {
+                                         double (&tot)[K], unsigned &epoch, int &parity,
+                                         Tail tail = Tail()) {
     block_sum_to_slot<K>(part, slot_of(sc, parity));
-    if (!scope_sync(sc, P.sync, epoch))
+    if (!scope_sync(sc, P.sync, epoch, false))
         return false;
-    grid_total<K>(slots_all(sc, parity), tot, sc.members);
+    grid_total<K>(slots_all(sc, parity), tot, sc.members, tail);
     parity ^= 1;
     return true;
 }
 
 // The same with float-pair arithmetic (per-iteration dot products).
-template <int K>
+template <int K, typename Tail = NoTail>
 __device__ __forceinline__ bool reduce_f(const SolveParams &P, const Scope &sc, FF (&part)[K],
-                                         double (&tot)[K], unsigned &epoch, int &parity) {
+                                         double (&tot)[K], unsigned &epoch, int &parity,
+                                         Tail tail = Tail()) {
     block_sum_ff<K>(part, reinterpret_cast<float2 *>(slot_of(sc, parity)));
-    if (!scope_sync(sc, P.sync, epoch))
+    if (!scope_sync(sc, P.sync, epoch, false))
         return false;
-    grid_total_ff<K>(reinterpret_cast<const float2 *>(slots_all(sc, parity)), tot, sc.members);
+    grid_total_ff<K>(reinterpret_cast<const float2 *>(slots_all(sc, parity)), tot, sc.members,
+                     tail);
     parity ^= 1;
     return true;
 }
@@ -700,8 +707,11 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
     constexpr bool defl = DEFL;   // a separate instantiation keeps the plain loop lean
     // per-warp slice pipeline: its mbarriers are set up once per solve
     SlicePipe pipe;
-    if constexpr (STG)
+    PipeGuard guard{nullptr, P.sync.timeout_ns};
+    if constexpr (STG) {
         pipe = pipe_open(A, warp, nwarps, lane);
+        guard.pp = &pipe;
+    }
     __shared__ MixedCtl ctl;
     const bool t0 = threadIdx.x == 0;
     unsigned epoch = 0;
@@ -788,6 +798,71 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
             return false;
     }
     __shared__ MixedState S;   // thread 0 only
+    // Thread 0's decisions.  They run in the tail of a reduction (see
+    // reduce_f), so the barrier that publishes the totals also publishes
+    // ctl: replace (1) with the next float unit, step (0) with a, bt, mu,
+    // or exit (2).
+    auto plan_replace = [&]() {
+        // The float unit sigma of the next period, a power of two near the
+        // residual's norm, chosen before the true residual is formed (from
+        // the recursive residual, or ||b|| at the start) so that one pass can
+        // store r and s in the new unit.  Powers of two scale float
+        // arithmetic exactly, so the choice only keeps the float values in
+        // range.
+        const double est = S.gamma > 0.0 && S.gamma < 1e300 ? S.sigma * sqrt(S.gamma) : sqrt(bn2);
+        const double sigma_new = exp2(rint(log2(est)));
+        const float f = (float)(S.sigma / sigma_new);
+        ctl.sigma_new = sigma_new;
+        ctl.f = f;
+        ctl.pf = P.restart ? 0.0f : f;
+        ctl.action = 1;
+    };
+    auto plan_step = [&]() {   // alpha, beta from fresh dot products
+        const double gamma = S.gamma;
+        double beta, denom;
+        if (S.fresh) {
+            beta = 0.0;
+            denom = S.delta;
+        } else {
+            beta = gamma / S.gamma_old;
+            denom = S.delta - beta * gamma / S.alpha_old;
+        }
+        if (defl)
+            denom -= S.eps * S.eps / cW;
+        if (!(denom > 0.0) || !(gamma > 0.0)) {
+            if (S.fresh) {
+                S.status = kDevNotSpd;
+                ctl.action = 2;
+            } else {
+                S.fresh = 1;   // replace, then restart
+                S.force = 1;
+                plan_replace();
+            }
+        } else {
+            S.fresh = 0;
+            const double alpha = gamma / denom;
+            ctl.action = 0;
+            ctl.a = (float)alpha;
+            ctl.bt = (float)beta;
+            ctl.mu = defl ? (float)(S.eps / cW) : 0.0f;
+            S.gamma_old = gamma;
+            S.alpha_old = alpha;
+        }
+    };
+    auto after_sweep = [&](const double (&t)[3]) {
+        S.gamma = t[0];
+        S.delta = t[1];
+        S.eps = t[2];
+        ++S.it;
+        ++S.since;
+        const bool trigger = S.force || (P.rr_period > 0 && S.since >= P.rr_period) ||
+                             (P.tau > 0.0 && S.gamma <= P.tau * P.tau * S.gamma_ref) ||
+                             S.ratio * S.gamma * S.sigma * S.sigma <= thr2 || S.it >= P.maxit;
+        if (trigger)
+            plan_replace();
+        else
+            plan_step();
+    };
     if (t0) {
         S.sigma = 1.0;
         S.ratio = 1.0;
@@ -799,30 +874,10 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
         S.fresh = 1;
         S.force = 1;
         ctl.sigma = 1.0;
+        plan_replace();
     }
+    __syncthreads();
     for (;;) {
-        if (t0) {
-            const bool trigger = S.force || (P.rr_period > 0 && S.since >= P.rr_period) ||
-                                 (P.tau > 0.0 && S.gamma <= P.tau * P.tau * S.gamma_ref) ||
-                                 S.ratio * S.gamma * S.sigma * S.sigma <= thr2 || S.it >= P.maxit;
-            ctl.action = trigger ? 1 : 0;
-            if (trigger) {
-                // The float unit sigma of the next period, a power of two near
-                // the residual's norm, chosen before the true residual is
-                // formed (from the recursive residual, or ||b|| at the start)
-                // so that one pass can store r and s in the new unit.  Powers
-                // of two scale float arithmetic exactly, so the choice only
-                // keeps the float values in range.
-                const double est = S.gamma > 0.0 && S.gamma < 1e300 ? S.sigma * sqrt(S.gamma)
-                                                                     : sqrt(bn2);
-                const double sigma_new = exp2(rint(log2(est)));
-                const float f = (float)(S.sigma / sigma_new);
-                ctl.sigma_new = sigma_new;
-                ctl.f = f;
-                ctl.pf = P.restart ? 0.0f : f;
-            }
-        }
-        __syncthreads();
         if (ctl.action == 1) {
             const double sig = ctl.sigma;
             // U1: fold the float correction into the FP64 solution
@@ -915,22 +970,20 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                     st_rows<R>(r + row0, rf);
                 }
             }
-            if (!reduce_d<2>(P, sc, part, tot, epoch, parity))
-                return false;
-            if (t0) {
+            auto after_residual = [&](const double (&t)[2]) {
                 ++S.reps;
-                S.rho = tot[1];
+                S.rho = t[1];
                 if (S.rho <= thr2) {
                     S.status = kDevOk;
                     ctl.action = 2;
                 } else if (S.it >= P.maxit) {
                     S.status = kDevNotConverged;
                     ctl.action = 2;
-                } else if (!(tot[0] > 0.0)) {
+                } else if (!(t[0] > 0.0)) {
                     S.status = kDevNotSpd;
                     ctl.action = 2;
                 } else {
-                    S.ratio = tot[1] / tot[0];
+                    S.ratio = t[1] / t[0];
                     if (P.restart)
                         S.fresh = 1;
                     else
@@ -938,8 +991,9 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                     S.sigma = ctl.sigma_new;
                     ctl.sigma = ctl.sigma_new;
                 }
-            }
-            __syncthreads();
+            };
+            if (!reduce_d<2>(P, sc, part, tot, epoch, parity, after_residual))
+                return false;
             if (ctl.action == 2)
                 break;
             // U3: w = Ahat r ; z = Ahat s ; p *= pf ; gamma, delta (, eps).
@@ -1000,54 +1054,24 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                     if (lane == 0)
                         atomicCAS(P.sync.err, 0, kDevTimeout);
                     pipe_drain(pipe, P.sync.timeout_ns);
+                } else {
+                    pipe_prime(A, pipe, range, warp, nwarps, lane);
                 }
             }
             FF fd[3] = {g0.ff(), g1.ff(), g2.ff()};
             double td[3];
-            if (!reduce_f<3>(P, sc, fd, td, epoch, parity))
-                return false;
-            if (t0) {
-                S.gamma = td[0];
-                S.delta = td[1];
-                S.eps = td[2];
-                S.gamma_ref = td[0];
+            auto after_replace = [&](const double (&t)[3]) {
+                S.gamma = t[0];
+                S.delta = t[1];
+                S.eps = t[2];
+                S.gamma_ref = t[0];
                 S.since = 0;
                 S.force = 0;
-            }
+                plan_step();
+            };
+            if (!reduce_f<3>(P, sc, fd, td, epoch, parity, after_replace))
+                return false;
         }
-        if (t0) {
-            const double gamma = S.gamma;
-            double beta, denom;
-            if (S.fresh) {
-                beta = 0.0;
-                denom = S.delta;
-            } else {
-                beta = gamma / S.gamma_old;
-                denom = S.delta - beta * gamma / S.alpha_old;
-            }
-            if (defl)
-                denom -= S.eps * S.eps / cW;
-            if (!(denom > 0.0) || !(gamma > 0.0)) {
-                if (S.fresh) {
-                    S.status = kDevNotSpd;
-                    ctl.action = 2;
-                } else {
-                    S.fresh = 1;
-                    S.force = 1;
-                    ctl.action = 1;   // replace, then restart
-                }
-            } else {
-                S.fresh = 0;
-                const double alpha = gamma / denom;
-                ctl.action = 0;
-                ctl.a = (float)alpha;
-                ctl.bt = (float)beta;
-                ctl.mu = defl ? (float)(S.eps / cW) : 0.0f;
-                S.gamma_old = gamma;
-                S.alpha_old = alpha;
-            }
-        }
-        __syncthreads();
         if (ctl.action == 2)
             break;
         if (ctl.action == 1)
@@ -1153,20 +1177,15 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                 if (lane == 0)
                     atomicCAS(P.sync.err, 0, kDevTimeout);
                 pipe_drain(pipe, P.sync.timeout_ns);
+            } else {
+                pipe_prime(A, pipe, range, warp, nwarps, lane);
             }
         }
         FF fp[3] = {g0.ff(), g1.ff(), g2.ff()};
         double tp[3];
-        if (!reduce_f<3>(P, sc, fp, tp, epoch, parity))
+        if (!reduce_f<3>(P, sc, fp, tp, epoch, parity, after_sweep))
             return false;
         wc ^= 1;
-        if (t0) {
-            S.gamma = tp[0];
-            S.delta = tp[1];
-            S.eps = tp[2];
-            ++S.it;
-            ++S.since;
-        }
     }
     unscale_pass<R>(P, sc, xh);
     if (t0)
