@@ -61,9 +61,10 @@ def source_digest():
     return h.hexdigest()
 
 
-def profiled_traffic():
+def profiled_traffic(slice_rows=None):
     """(dram bytes per launch, iterations) from the committed ncu summary, or
-    None when the kernel sources changed since that capture."""
+    None when the kernel sources changed since that capture or it was taken
+    with another slice height."""
     try:
         fields = {}
         with open(PROFILE) as f:
@@ -72,6 +73,8 @@ def profiled_traffic():
                     k, v = line[2:].split(":", 1)
                     fields[k.strip()] = v.strip().strip("`")
         if fields.get("source_sha256") != source_digest():
+            return None
+        if slice_rows is not None and int(fields.get("slice_rows", -1)) != slice_rows:
             return None
         return float(fields["dram_bytes_per_launch"]), int(fields["iterations"])
     except (OSError, KeyError, ValueError):
@@ -235,7 +238,7 @@ def run_ours(args):
     s = lc.config2(s=args.size, seed=0)
     n, F = s.n, s.nfaces
     # each solver at its own best layout (autotuned once, cached; untimed)
-    cands = (args.slice_rows,) if args.slice_rows else (64, 128)
+    cands = (args.slice_rows,) if args.slice_rows else (128, 64)
     fixed = {"rr_period": args.rr_period} if args.rr_period else {}
     if args.slice_rows and args.rr_period:
         tune_m = {"slice_rows": args.slice_rows, "rr_period": args.rr_period}   # fixed: no tuning
@@ -317,7 +320,7 @@ def run_ours(args):
     col_bytes = 2 if (A.info()["col16"] and grid["staged"]) else 4
     alg_bytes = bytes_mixed(n, F, it, reps, col_bytes)
     achieved = alg_bytes / statistics.median(t_mixed) / 1e9
-    prof = profiled_traffic()
+    prof = profiled_traffic(A.info()["slice_rows"])
     traffic = None
     if prof is not None and prof[1] == it:
         traffic = prof[0]
