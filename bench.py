@@ -239,12 +239,14 @@ def run_ours(args):
     n, F = s.n, s.nfaces
     # each solver at its own best layout (autotuned once, cached; untimed)
     cands = (args.slice_rows,) if args.slice_rows else (128, 64)
-    fixed = {"rr_period": args.rr_period} if args.rr_period else {}
+    fixed = {"rr_period": args.rr_period, "tau": args.tau} if args.rr_period else {}
     if args.slice_rows and args.rr_period:
-        tune_m = {"slice_rows": args.slice_rows, "rr_period": args.rr_period}   # fixed: no tuning
+        tune_m = dict(slice_rows=args.slice_rows, **fixed)   # fixed: no tuning
     else:
         tune_m = autotune.tune_single(s, "mixed", tol=TOL, slice_rows=cands, **fixed)
-    rr_m = args.rr_period or tune_m.get("rr_period", 12)
+    # replacement rule: the tuned one, else the library's default (both 0)
+    rr_m = args.rr_period or tune_m.get("rr_period", 0)
+    tau_m = args.tau if args.rr_period else tune_m.get("tau", 0.0)
     handles = {}
 
     def handle(C):
@@ -280,12 +282,13 @@ def run_ours(args):
         return times, outs
 
     def mixed():
-        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="mixed", rr_period=rr_m)
+        _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="mixed", rr_period=rr_m,
+                                         tau=tau_m)
         return st, it, rr, A.stats()["replacements"]
 
     def mixed_deflated():
         _, st, it, rr = pkg.pipecg_solve(A, b, x, tol=TOL, precision="mixed", rr_period=rr_m,
-                                         deflate=True)
+                                         tau=tau_m, deflate=True)
         return st, it, rr, A.stats()["replacements"]
 
     A_pcg = A_pipe = A
@@ -376,7 +379,7 @@ def run_ours(args):
     def e2e_step():
         bd.copy_(hb, non_blocking=True)
         x.zero_()
-        pkg.pipecg_solve(A, bd, x, tol=TOL, precision="mixed", rr_period=rr_m)
+        pkg.pipecg_solve(A, bd, x, tol=TOL, precision="mixed", rr_period=rr_m, tau=tau_m)
         hx.copy_(x, non_blocking=True)
         return None
 
@@ -410,7 +413,7 @@ def run_ours(args):
                    "cells": n, "faces": F, "slice_rows": A.info()["slice_rows"],
                    "blocks_per_sm": args.blocks_per_sm, "staging": args.staging,
                    "grid_blocks": grid["grid_blocks"], "block_threads": grid["block_threads"],
-                   "rr_period": rr_m, "l2": "256 MB flush before every step",
+                   "rr_period": rr_m, "tau": tau_m, "l2": "256 MB flush before every step",
                    "parallelism": "replicas" if world > 1 else "single"},
         "solve": {"status": st, "iters": it, "replacements": reps, "relres": rr,
                   "relres_oracle": relres_oracle},
@@ -497,6 +500,7 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--staging", type=int, default=0, choices=[0, -1])
     ap.add_argument("--rr-period", type=int, default=0)
+    ap.add_argument("--tau", type=float, default=0.0)
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")

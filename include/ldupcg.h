@@ -81,10 +81,11 @@ typedef struct pcg_opts {
     int rr_period;          /* iterations between residual replacements:
                                LDU_FP64 default 0 (replace only when the
                                recursive residual reaches tol);
-                               LDU_MIXED default 12 (FP64 replacement) */
+                               LDU_MIXED: when rr_period and tau are both 0,
+                               16 with tau 0.3 (FP64 replacement) */
     double tau;             /* LDU_MIXED: also replace when (r, M^-1 r) has
                                dropped by tau^2 since the last replacement;
-                               0 = off (default) */
+                               0 = off (0.3 when rr_period is 0 too) */
     int restart;            /* LDU_MIXED: 1 = every replacement restarts the
                                search (classic defect correction with inner
                                tolerance tau); 0 = keep the search directions

@@ -67,13 +67,15 @@ def _time(call, repeats):
     return best
 
 
-RR_PERIODS = (12, 16)
+# (replacement period, tau) pairs tried for the mixed solve
+RR_RULES = ((16, 0.3), (16, 0.2), (14, 0.0), (12, 0.0), (20, 0.3))
 
 
 def tune_single(system, precision="mixed", tol=1e-8, repeats=2, use_cache=True,
                 slice_rows=SLICE_ROWS, **solve_kw):
-    """Best slice height (and, for the mixed solve, replacement period) for
-    pcg_solve ('pcg') / pipecg_solve ('fp64', 'mixed') on this system."""
+    """Best slice height (and, for the mixed solve, replacement period and
+    tau) for pcg_solve ('pcg') / pipecg_solve ('fp64', 'mixed') on this
+    system."""
     key = _key("single", [system.n], [system.nfaces],
                dict(precision=precision, tol=tol, slice_rows=list(slice_rows), **solve_kw))
     if use_cache:
@@ -82,14 +84,15 @@ def tune_single(system, precision="mixed", tol=1e-8, repeats=2, use_cache=True,
             return hit
     b = torch.as_tensor(system.b, device="cuda")
     x = torch.zeros_like(b)
-    periods = RR_PERIODS if precision == "mixed" and "rr_period" not in solve_kw else (None,)
+    rules = (RR_RULES if precision == "mixed" and "rr_period" not in solve_kw
+             and "tau" not in solve_kw else (None,))
     results = []
     for C in slice_rows:
         A = ldupcg.from_system(system, slice_rows=C)
-        for rr in periods:
+        for rule in rules:
             kw = dict(solve_kw)
-            if rr is not None:
-                kw["rr_period"] = rr
+            if rule is not None:
+                kw["rr_period"], kw["tau"] = rule
 
             def call():
                 x.zero_()
@@ -99,8 +102,8 @@ def tune_single(system, precision="mixed", tol=1e-8, repeats=2, use_cache=True,
                     ldupcg.pipecg_solve(A, b, x, tol=tol, precision=precision, **kw)
 
             res = {"slice_rows": C, "seconds": _time(call, repeats)}
-            if rr is not None:
-                res["rr_period"] = rr
+            if rule is not None:
+                res["rr_period"], res["tau"] = rule
             results.append(res)
         A.close()
     best = min(results, key=lambda r: r["seconds"])

@@ -94,10 +94,14 @@ const void *pick_kernel(const ldu_matrix *A, Kind k, bool stg) {
     }
 }
 
-// Default iterations between FP64 residual replacements of the mixed solve:
-// on the 128^3 lognormal case 12 keeps the FP64 method's iteration count
-// (755 against 752), 16 loses 12 % of it to a plateau near convergence.
-constexpr int kMixedPeriod = 12;
+// Default replacement rule of the mixed solve: every 16 float iterations,
+// and sooner once (r, r) has dropped by 0.3^2.  Measured on the 64^3, 96^3
+// and 128^3 lognormal cases it keeps the FP64 method's iteration counts
+// (417, 616, 752) with 29, 41 and 50 replacements; every 12 needs 36, 53
+// and 64, and every 16 without the drop test loses 12 % of the iterations
+// at 128^3 to a plateau near convergence.
+constexpr int kMixedPeriod = 16;
+constexpr double kMixedTau = 0.3;
 
 // Largest dynamic shared memory a block of the staged mixed kernel may take
 // and still leave room for minb resident blocks per SM (228 KB per SM, less
@@ -127,8 +131,10 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     if (opt.rr_period < 0 || opt.tau < 0.0 || opt.barrier_timeout_s < 0.0 ||
         (opt.deflate != 0 && opt.deflate != 1))
         return LDU_ERR_BAD_ARG;
-    if (kind == kMixed && opt.rr_period == 0 && opt.tau == 0.0)
+    if (kind == kMixed && opt.rr_period == 0 && opt.tau == 0.0) {
         opt.rr_period = kMixedPeriod;
+        opt.tau = kMixedTau;
+    }
     A->last = ldu_solve_stats{};
     if (A->n == 0) {
         if (iters)

@@ -535,7 +535,7 @@ int pcg_solve_batched_async(const ldu_matrix *Ac, const double *b, double *x, do
         (opt.deflate != 0 && opt.deflate != 1))
         return LDU_ERR_BAD_ARG;
     if (precision == LDU_MIXED && opt.rr_period == 0 && opt.tau == 0.0)
-        opt.rr_period = 12;   // as the single-system default
+        opt.rr_period = 12;   // small systems: a plain period of 12
     cudaStream_t st = (cudaStream_t)stream;
     const void *kern = batch_kernel(A->C, precision, precision == LDU_MIXED && opt.deflate);
     SolveParams P;

@@ -141,7 +141,7 @@ def test_pipecg_fp64_parity(pkg, oracle_mod, case):
 
 @pytest.mark.parametrize("case", list(SOLVE_CASES))
 @pytest.mark.parametrize("mode", [dict(rr_period=16), dict(rr_period=0, tau=1e-3, restart=True),
-                                  dict(rr_period=16, deflate=True)])
+                                  dict(rr_period=16, deflate=True), dict(rr_period=16, tau=0.3)])
 def test_mixed_parity(pkg, oracle_mod, case, mode):
     s = SOLVE_CASES[case]()
     A = pkg.from_system(s)
@@ -160,6 +160,20 @@ def test_mixed_parity(pkg, oracle_mod, case, mode):
     err = np.linalg.norm(xh - xs) / np.linalg.norm(xs)
     err_ref = np.linalg.norm(ref.x - xs) / np.linalg.norm(xs)
     assert err <= max(10 * err_ref, 1e-6)
+    A.close()
+
+
+def test_mixed_default_rule_is_period_16_tau_03(pkg):
+    """With rr_period and tau both 0 the mixed solve replaces every 16
+    iterations and on a 0.3^2 drop: bitwise the same run as those options."""
+    s = lc.config2(s=24)
+    A = pkg.from_system(s, slice_rows=64)
+    b = cuda(s.b)
+    x0, st0, it0, rr0 = pkg.pipecg_solve(A, b, tol=1e-9, precision="mixed")
+    reps0 = A.stats()["replacements"]
+    x1, st1, it1, rr1 = pkg.pipecg_solve(A, b, tol=1e-9, precision="mixed", rr_period=16, tau=0.3)
+    assert st0 == st1 == 0 and it0 == it1 and reps0 == A.stats()["replacements"]
+    assert torch.equal(x0, x1) and rr0 == rr1
     A.close()
 
 
