@@ -475,7 +475,9 @@ def run_batched(args, dev, pkg, timed_fn):
     t_sep = timed_fn(separate, 1, 1, prep=x.zero_)
     for Ak in handles:
         Ak.close()
-    alg = sum(bytes_mixed(s.n, s.nfaces, int(its[k]), int(its[k]) // rr_b + 2)
+    staged_b = int(A.stats()["staged"])
+    cb = 2 if (A.info()["col16"] and staged_b) else 4
+    alg = sum(bytes_mixed(s.n, s.nfaces, int(its[k]), int(its[k]) // rr_b + 2, cb)
               for k, s in enumerate(systems))
     tb = statistics.median(t_batch)
     A.close()
@@ -485,6 +487,7 @@ def run_batched(args, dev, pkg, timed_fn):
             "max_relres": float(rrs.max()), "alg_gbs": alg / tb / 1e9,
             "tuned": {k: best[k] for k in ("slice_rows", "max_team", "team_work_scale")},
             "grid_blocks": info["grid_blocks"], "teams_max": info["max_team"],
+            "staged": staged_b,
             "ntasks": info["ntasks"]}
 
 

@@ -905,14 +905,25 @@ struct PipeGuard {
     }
 };
 
+// Column of a staged slot of row `row`, clamped into the padded matrix: one
+// unsigned min per gather (about 1 % of the solve), so that no value read
+// from shared memory can address outside the vectors.  A correct stage is
+// never clamped.
+template <typename CT>
+__device__ __forceinline__ int staged_col(int c, int row, int n_pad) {
+    if constexpr (sizeof(CT) == 2)
+        c += row;
+    return (int)min((unsigned)c, (unsigned)(n_pad - 1));
+}
+
 // acc[j] += sum_k val * x[col] for this lane's R rows, slots taken from a
 // staged slice in shared memory (same order of operations as sell_accum);
 // KS slots' gathers are in flight per batch.  CT = short: the stage holds
 // column minus row, and row0 is the lane's first row.
 template <int R, int KS, typename CT>
 __device__ __forceinline__ void sell_accum_staged(const char *stage, unsigned val_off, int w, int C,
-                                                  int lane, int row0, const float *__restrict__ x,
-                                                  float (&acc)[R]) {
+                                                  int lane, int row0, int n_pad,
+                                                  const float *__restrict__ x, float (&acc)[R]) {
     const CT *scol = reinterpret_cast<const CT *>(stage);
     const float *sval = reinterpret_cast<const float *>(stage + val_off);
     for (int k0 = 0; k0 < w; k0 += KS) {
@@ -923,11 +934,8 @@ __device__ __forceinline__ void sell_accum_staged(const char *stage, unsigned va
                 int c[R];
                 ld_rows<R>(scol + (k0 + k) * C + R * lane, c);
 #pragma unroll
-                for (int j = 0; j < R; ++j) {
-                    if constexpr (sizeof(CT) == 2)
-                        c[j] += row0 + j;
-                    g[k][j] = x[c[j]];
-                }
+                for (int j = 0; j < R; ++j)
+                    g[k][j] = x[staged_col<CT>(c[j], row0 + j, n_pad)];
             }
 #pragma unroll
         for (int k = 0; k < KS; ++k)
@@ -945,7 +953,7 @@ __device__ __forceinline__ void sell_accum_staged(const char *stage, unsigned va
 // acc2 += Ahat x2), in slot order.
 template <int R, int KS, typename CT>
 __device__ __forceinline__ void sell_accum2_staged(const char *stage, unsigned val_off, int w, int C,
-                                                   int lane, int row0,
+                                                   int lane, int row0, int n_pad,
                                                    const float *__restrict__ x1,
                                                    const float *__restrict__ x2, float (&acc1)[R],
                                                    float (&acc2)[R]) {
@@ -960,10 +968,9 @@ __device__ __forceinline__ void sell_accum2_staged(const char *stage, unsigned v
                 ld_rows<R>(scol + (k0 + k) * C + R * lane, c);
 #pragma unroll
                 for (int j = 0; j < R; ++j) {
-                    if constexpr (sizeof(CT) == 2)
-                        c[j] += row0 + j;
-                    g1[k][j] = x1[c[j]];
-                    g2[k][j] = x2[c[j]];
+                    const int cj = staged_col<CT>(c[j], row0 + j, n_pad);
+                    g1[k][j] = x1[cj];
+                    g2[k][j] = x2[cj];
                 }
             }
 #pragma unroll

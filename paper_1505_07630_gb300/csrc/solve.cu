@@ -220,6 +220,8 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     int status;
     if (flags_err[0] == kDevTimeout)
         status = LDU_ERR_BARRIER_TIMEOUT;
+    else if (flags_err[0] != 0)
+        status = LDU_ERR_CUDA;
     else if (flags_err[1] & (kFlagBadDiag | kFlagNonFinite))
         status = LDU_ERR_NOT_SPD;
     else

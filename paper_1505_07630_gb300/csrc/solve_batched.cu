@@ -65,10 +65,15 @@ __device__ __forceinline__ Scope task_scope(const SolveParams &P, const BatchVie
     return sc;
 }
 
-template <int R, int KB, bool DEFL>
+template <int R, int KB, bool DEFL, bool STG = false>
 __global__ void __launch_bounds__(256, 2) k_mixed_batched(SolveParams P, BatchView B) {
+    // one pipeline for all the block's systems: its mbarriers are set up once
+    SlicePipe pipe;
+    if constexpr (STG)
+        pipe = pipe_open(P.A, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31);
     for (int e = B.list_begin[blockIdx.x]; e < B.list_begin[blockIdx.x + 1]; ++e)
-        if (!mixed_body<R, KB, DEFL>(P, task_scope(P, B, B.list[e])))
+        if (!mixed_body<R, KB, DEFL, STG, StagedBatch<R, 2>::ks>(P, task_scope(P, B, B.list[e]),
+                                                                  &pipe))
             return;
 }
 
@@ -169,6 +174,9 @@ struct BatchKernels {
         return defl ? (const void *)k_mixed_batched<R, Batch<R>::mixed, true>
                     : (const void *)k_mixed_batched<R, Batch<R>::mixed, false>;
     }
+    static const void *mixed_staged() {
+        return (const void *)k_mixed_batched<R, Batch<R>::mixed, false, true>;
+    }
     static const void *pcg() { return (const void *)k_pcg64_batched<R, Batch<R>::pcg>; }
 };
 
@@ -177,6 +185,18 @@ const void *batch_kernel(int C, int precision, bool defl) {
         return C == 32 ? BatchKernels<1>::pcg() : (C == 64 ? BatchKernels<2>::pcg() : BatchKernels<4>::pcg());
     return C == 32 ? BatchKernels<1>::mixed(defl)
                    : (C == 64 ? BatchKernels<2>::mixed(defl) : BatchKernels<4>::mixed(defl));
+}
+
+// the mixed kernel whose float sweeps stage the matrix in shared memory
+const void *batch_kernel_staged(int C) {
+    return C == 32 ? BatchKernels<1>::mixed_staged()
+                   : (C == 64 ? BatchKernels<2>::mixed_staged() : BatchKernels<4>::mixed_staged());
+}
+
+// dynamic shared memory of the staged kernel for meta_bytes of slice metadata
+size_t batch_staged_smem(const ldu_matrix *A, size_t meta_bytes) {
+    return staged_smem_bytes((int)(meta_bytes / sizeof(int2)), A->block_threads / 32, A->max_w,
+                             A->C, A->col16 ? 2 : 4, 2);
 }
 
 }  // namespace
@@ -195,6 +215,7 @@ struct ldu_batch {
     int ntasks;
     int grid;
     size_t smem;
+    bool staged;      // the mixed solve may use the staged kernel
     int max_team_used;
     batch_opts opts;
 };
@@ -448,6 +469,22 @@ int ldu_create_batched(int nsys, const int64_t *n, const int64_t *nFaces, const 
             goto fail;
         }
         Bt->grid = per_sm * A->num_sms;
+        // staged float sweeps, when the staged kernel keeps the same number of
+        // blocks per SM co-resident with its largest shared memory
+        Bt->staged = false;
+        if (A->staging == 0 && A->max_w > 0) {
+            const void *ks = batch_kernel_staged(C);
+            const size_t sm = batch_staged_smem(A, kMetaSmemMax);
+            int ps = 0;
+            if (sm <= (size_t)228 * 1024 / (size_t)per_sm - 5 * 1024 &&
+                cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
+                    cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, ks, A->block_threads, sm) ==
+                    cudaSuccess &&
+                ps >= per_sm)
+                Bt->staged = true;
+            cudaGetLastError();   // a refused attribute or query only turns staging off
+        }
     }
     A->batch = Bt;
     {
@@ -537,12 +574,16 @@ int pcg_solve_batched_async(const ldu_matrix *Ac, const double *b, double *x, do
     if (precision == LDU_MIXED && opt.rr_period == 0 && opt.tau == 0.0)
         opt.rr_period = 12;   // small systems: a plain period of 12
     cudaStream_t st = (cudaStream_t)stream;
-    const void *kern = batch_kernel(A->C, precision, precision == LDU_MIXED && opt.deflate);
+    const bool defl = precision == LDU_MIXED && opt.deflate;
+    const bool stg = precision == LDU_MIXED && !defl && Bt->staged;
+    const void *kern = stg ? batch_kernel_staged(A->C) : batch_kernel(A->C, precision, defl);
+    const size_t smem = stg ? batch_staged_smem(A, Bt->smem) : Bt->smem;
     SolveParams P;
     P.A = view_of(A);
     P.A.meta_smem = Bt->smem > 0;
     P.A.meta_cap = (int)(Bt->smem / sizeof(int2));
-    P.A.stage_w = 0;
+    P.A.stage_w = stg ? A->max_w : 0;
+    P.A.stages = stg ? 2 : 0;
     P.sync.count = A->bar_count;
     P.sync.err = A->bar_err;
     const double tmo = opt.barrier_timeout_s > 0.0 ? opt.barrier_timeout_s : 10.0;
@@ -578,7 +619,7 @@ int pcg_solve_batched_async(const ldu_matrix *Ac, const double *b, double *x, do
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(Bt->grid);
     cfg.blockDim = dim3(A->block_threads);
-    cfg.dynamicSmemBytes = Bt->smem;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -586,6 +627,9 @@ int pcg_solve_batched_async(const ldu_matrix *Ac, const double *b, double *x, do
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     e = cudaLaunchKernelExC(&cfg, kern, args);
+    A->last.staged = stg ? 1 : 0;
+    A->last.grid_blocks = Bt->grid;
+    A->last.block_threads = A->block_threads;
     return cuda_status(e);
 }
 
@@ -603,6 +647,8 @@ int ldu_batch_results(const ldu_matrix *A, int *iters, double *relres, int *stat
         return cuda_status(e);
     if (err == kDevTimeout)
         return LDU_ERR_BARRIER_TIMEOUT;
+    if (err != 0)
+        return LDU_ERR_CUDA;
     int worst = LDU_OK;
     for (int k = 0; k < Bt->nsys; ++k) {
         const SolveOut &o = Bt->out_host[k];

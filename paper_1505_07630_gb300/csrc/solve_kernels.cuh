@@ -694,8 +694,12 @@ struct StagedBatch {
     static constexpr int ks = MINB == 2 ? (R == 1 ? 6 : 1) : (R == 1 ? (MINB == 4 ? 3 : 6) : 2);
 };
 
+// pipe_in: the block's slice pipeline (STG), opened once per launch by the
+// kernel, so that a block solving several systems in turn never
+// re-initialises a live mbarrier
 template <int R, int KB, bool DEFL, bool STG = false, int SKS = 6>
-__device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc) {
+__device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc,
+                                           SlicePipe *pipe_in = nullptr) {
     __syncthreads();   // the previous body of this block is done with shared state
     LANE_ROWS;
     load_slice_meta(P.A, sc.range);
@@ -706,12 +710,10 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
     float *w0f = P.v32[7], *q0f = P.v32[8], *t0f = P.v32[9];
     constexpr bool defl = DEFL;   // a separate instantiation keeps the plain loop lean
     // per-warp slice pipeline: its mbarriers are set up once per solve
-    SlicePipe pipe;
-    PipeGuard guard{nullptr, P.sync.timeout_ns};
-    if constexpr (STG) {
-        pipe = pipe_open(A, warp, nwarps, lane);
-        guard.pp = &pipe;
-    }
+    SlicePipe unused;
+    SlicePipe &pipe = STG ? *pipe_in : unused;
+    // drains this body's copies on every exit path
+    PipeGuard guard{STG ? pipe_in : nullptr, P.sync.timeout_ns};
     __shared__ MixedCtl ctl;
     const bool t0 = threadIdx.x == 0;
     unsigned epoch = 0;
@@ -1021,11 +1023,13 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                     }
                     const int ws = slice_meta(A, s, range).y;
                     if (A.col16)
-                        sell_accum2_staged<R, (SKS + 1) / 2, short>(stage, pipe.val_off, ws, A.C, lane, row0,
-                                                          r, sv, aw, az);
+                        sell_accum2_staged<R, (SKS + 1) / 2, short>(
+                            stage, pipe.val_off, ws, A.C, lane, row0, A.n_pad, r, sv,
+                            aw, az);
                     else
-                        sell_accum2_staged<R, (SKS + 1) / 2, int>(stage, pipe.val_off, ws, A.C, lane, row0,
-                                                        r, sv, aw, az);
+                        sell_accum2_staged<R, (SKS + 1) / 2, int>(
+                            stage, pipe.val_off, ws, A.C, lane, row0, A.n_pad, r, sv,
+                            aw, az);
                     pipe_pop(A, pipe, range, nwarps, lane);
                 } else {
                     sell_accum2<float, R, KB>(A, slice_meta(A, s, range), lane, r, sv, aw, az);
@@ -1123,10 +1127,11 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
                 }
                 const int ws = slice_meta(A, s, range).y;
                 if (A.col16)
-                    sell_accum_staged<R, SKS, short>(stage, pipe.val_off, ws, A.C, lane, row0, w,
-                                                     nn);
+                    sell_accum_staged<R, SKS, short>(stage, pipe.val_off, ws, A.C, lane, row0,
+                                                     A.n_pad, w, nn);
                 else
-                    sell_accum_staged<R, SKS, int>(stage, pipe.val_off, ws, A.C, lane, row0, w, nn);
+                    sell_accum_staged<R, SKS, int>(stage, pipe.val_off, ws, A.C, lane, row0,
+                                                   A.n_pad, w, nn);
                 pipe_pop(A, pipe, range, nwarps, lane);
             } else {
                 sell_accum<float, R, KB>(A, slice_meta(A, s, range), lane, w, nn);
@@ -1200,7 +1205,10 @@ __global__ void __launch_bounds__(256, MINB) k_mixed(SolveParams P) {
     const Scope sc = grid_scope(P);
     // the deflated loop carries three more vectors: fewer gathers in flight
     constexpr int ks = DEFL ? (StagedBatch<R, MINB>::ks + 1) / 2 : StagedBatch<R, MINB>::ks;
-    mixed_body<R, KB, DEFL, STG, ks>(P, sc);
+    SlicePipe pipe;
+    if constexpr (STG)
+        pipe = pipe_open(P.A, threadIdx.x >> 5, blockDim.x >> 5, threadIdx.x & 31);
+    mixed_body<R, KB, DEFL, STG, ks>(P, sc, &pipe);
 }
 
 }  // namespace

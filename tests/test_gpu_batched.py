@@ -48,10 +48,13 @@ def split(x, systems):
 
 
 @pytest.mark.parametrize("C", [32, 64, 128])
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batched_parity(pkg, oracle_mod, C, precision):
+@pytest.mark.parametrize("precision,staging", [("fp64", 0), ("mixed", 0), ("mixed", -1)])
+def test_batched_parity(pkg, oracle_mod, C, precision, staging):
+    """staging 0: the mixed solve's float sweeps stage the matrix in shared
+    memory (each one-block team opens and drains its own pipeline per
+    system); -1: plain loads."""
     systems = small_batch()
-    A = pkg.from_systems(systems, slice_rows=C)
+    A = pkg.from_systems(systems, slice_rows=C, staging=staging)
     b = cat_b(systems)
     x, worst, its, rrs, sts = pkg.pcg_solve_batched(A, b, tol=1e-8, precision=precision)
     assert worst == 0 and np.all(sts == 0)
