@@ -167,6 +167,49 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# ---- ranks (one process per GPU; replicas: no collective on the data path) --
+class Ranks:
+    """Rank layout of a torchrun launch, or of a single process."""
+
+    def __init__(self, env=None):
+        env = os.environ if env is None else env
+        self.world = int(env.get("WORLD_SIZE", "1"))
+        self.rank = int(env.get("RANK", "0"))
+        self.local = int(env.get("LOCAL_RANK", "0"))
+
+
+def init_ranks(backend):
+    """(ranks, process group module or None): the group is set up only for
+    more than one rank, from the MASTER_* variables torchrun exports."""
+    r = Ranks()
+    dist = None
+    if r.world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+    return r, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def job_seconds(local_seconds, dist, device="cpu"):
+    """The job's time: the largest of every rank's own timed total."""
+    if dist is None:
+        return local_seconds
+    import torch
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def emit(line, ranks):
+    """Rank 0 prints the one JSON line of the run."""
+    if ranks.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ---- the oracle arm --------------------------------------------------------
 def oracle_sample(sys_, iters_cap):
     """Seconds per FP64 PCG iteration of the oracle over a capped run."""
@@ -178,9 +221,9 @@ def oracle_sample(sys_, iters_cap):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
+    ranks = Ranks()
+    if ranks.rank != 0:
+        return   # the oracle arm runs on rank 0 alone; other ranks exit without work
     import ldu_cases as lc
     import oracle
     s = lc.config2(s=args.size, seed=0)
@@ -209,7 +252,7 @@ def run_reference(args):
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "oracle_iters": full.iters, "oracle_relres": full.relres,
     }
-    print(json.dumps(line))
+    emit(line, ranks)
 
 
 # ---- our arm ---------------------------------------------------------------
@@ -219,13 +262,8 @@ def run_ours(args):
 
     import ldu_cases as lc
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    ranks, dist = init_ranks("nccl")
+    world, rank, local = ranks.world, ranks.rank, ranks.local
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -304,18 +342,14 @@ def run_ours(args):
         _, st, it, rr = pkg.pipecg_solve(A_pipe, b, x, tol=TOL, precision="fp64")
         return st, it, rr, A_pipe.stats()["replacements"]
 
-    if dist is not None:
-        dist.barrier()
+    barrier(dist)
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
         t_mixed, o_mixed = timed(mixed, args.steps, args.warmup)
+    torch.cuda.synchronize(dev)
+    barrier(dist)
     x_mixed = x.cpu().numpy()
-    if dist is not None:
-        tt = torch.tensor([sum(t_mixed)], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt)
-    else:
-        total = sum(t_mixed)
+    total = job_seconds(sum(t_mixed), dist, dev)
     st, it, rr, reps = o_mixed[-1]
     grid = A.stats()
     step_s = total / args.steps
@@ -384,7 +418,7 @@ def run_ours(args):
         return None
 
     t_e2e, _ = timed(e2e_step, args.steps, 1)
-    e2e_s = statistics.mean(t_e2e)
+    e2e_s = job_seconds(statistics.mean(t_e2e), dist, dev)
 
     batched = None
     if not args.skip_batched:
@@ -431,8 +465,7 @@ def run_ours(args):
         "batched": batched,
     }
     line.update(extra)
-    if rank == 0:
-        print(json.dumps(line))
+    emit(line, ranks)
     for h in handles.values():
         h.close()
     if dist is not None:
