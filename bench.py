@@ -423,6 +423,10 @@ def run_ours(args):
     batched = None
     if not args.skip_batched:
         batched = run_batched(args, dev, pkg, timed_fn=timed_generic)
+    pressure = autograd_case = None
+    if not args.skip_extra:
+        pressure = run_pressure(args, dev, pkg, timed_fn=timed_generic)
+        autograd_case = run_autograd(args, dev, pkg, timed_fn=timed_generic)
 
     # CPU baseline: the oracle on this host, bounded sample, rank 0 only
     cpu = None
@@ -463,6 +467,8 @@ def run_ours(args):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "batched": batched,
+        "pressure256": pressure,
+        "differentiable": autograd_case,
     }
     line.update(extra)
     emit(line, ranks)
@@ -524,6 +530,71 @@ def run_batched(args, dev, pkg, timed_fn):
             "ntasks": info["ntasks"]}
 
 
+def run_pressure(args, dev, pkg, timed_fn):
+    """The icoFoam-style pressure system on a graded 256³ box (pure Neumann,
+    one pinned cell): mixed pipelined PCG with constant-vector deflation
+    against FP64 Jacobi-PCG, both to 1e-8, slice height 128."""
+    import torch
+
+    import ldu_cases as lc
+
+    s = lc.config3(s=256, seed=0)
+    A = pkg.from_system(s, device=dev, slice_rows=128)
+    b = torch.as_tensor(s.b, device=dev)
+    x = torch.zeros_like(b)
+    out = {"cells": s.n, "faces": s.nfaces}
+
+    def mixed():
+        pkg.pipecg_solve(A, b, x, tol=TOL, maxit=50000, precision="mixed", deflate=True)
+
+    def pcg():
+        pkg.pcg_solve(A, b, x, tol=TOL, maxit=50000)
+
+    for name, call in (("mixed_deflated", mixed), ("fp64_pcg", pcg)):
+        t = timed_fn(call, 2, 1, prep=x.zero_)
+        st = A.stats()
+        out[name] = {"s": statistics.median(t), "iters": st["iters"],
+                     "replacements": st["replacements"], "relres": st["relres"],
+                     "status": st["status"]}
+    out["speedup_mixed_vs_fp64_pcg"] = out["fp64_pcg"]["s"] / out["mixed_deflated"]["s"]
+    A.close()
+    return out
+
+
+def run_autograd(args, dev, pkg, timed_fn):
+    """Differentiable solve on a 64³ mesh, batch of 8 diffusivity fields:
+    loss 0.5 ||x(c) - x_t||², forward solve plus backward (adjoint solve and
+    face/diagonal/RHS gradients) in one batched handle, mixed precision to
+    1e-10; targets from FP64 solves of the reference fields."""
+    import numpy as np
+    import torch
+
+    import ldu_cases as lc
+
+    systems, refs = lc.config5()
+    Ar = pkg.from_systems(refs, device=dev)
+    br = torch.as_tensor(np.concatenate([r.b for r in refs]), device=dev)
+    xt, *_ = pkg.pcg_solve_batched(Ar, br, tol=1e-12, precision="fp64")
+    Ar.close()
+    A = pkg.from_systems(systems, device=dev)
+    cat = lambda name: torch.as_tensor(np.concatenate([getattr(q, name) for q in systems]),  # noqa: E731
+                                       device=dev)
+    coef, extra, b = cat("coef"), cat("diag_extra"), cat("b")
+
+    def step():
+        c = coef.clone().requires_grad_(True)
+        bb = b.clone().requires_grad_(True)
+        xs = pkg.ldu_solve(A, c, extra, bb, precision="mixed", tol=1e-10)
+        loss = 0.5 * ((xs - xt) ** 2).sum()
+        loss.backward()
+        return c.grad
+
+    t = timed_fn(step, 2, 1)
+    A.close()
+    return {"systems": len(systems), "cells_each": systems[0].n,
+            "faces_each": systems[0].nfaces, "forward_backward_s": statistics.median(t)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -541,6 +612,8 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="skip the 256^3 pressure and differentiable-solve timings")
     ap.add_argument("--batch-systems", type=int, default=512)
     ap.add_argument("--print-digest", action="store_true")
     args = ap.parse_args()
