@@ -190,7 +190,11 @@ int pcg_solve(const ldu_matrix *A, const double *b, double *x, double tol, int m
  *              the recursive residual reaches tol (and every rr_period steps);
  *              LDU_MIXED: the recurrences in float on a float copy of the
  *              matrix; the solution accumulates in double and the residual
- *              is replaced by the double b - A x every rr_period steps.
+ *              is replaced by the double b - A x every rr_period steps and
+ *              whenever (r, M^-1 r) has dropped by tau^2 (opts; by default
+ *              every 16 steps or on a 0.3^2 drop).  Convergence is only
+ *              declared on such a double residual.  deflate = 1 adds the
+ *              constant-vector deflation for singular-ish pressure systems.
  *   opts       host, may be NULL
  * Other arguments as pcg_solve.  A non-positive pipelined denominator is
  * treated as rounding drift (replace and restart); only a non-positive

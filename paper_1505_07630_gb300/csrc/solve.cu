@@ -22,7 +22,10 @@
 //           w is double-buffered because neighbours gather it while it is
 //           rewritten.  Residual replacement: 3 passes.
 //   mixed   the same pipelined sweep in float; FP64 holds the solution and
-//           the periodic true residual (4 passes per replacement).
+//           the periodic true residual (3 passes per replacement: fold the
+//           float correction into x; true residual together with s = Ahat p;
+//           w = Ahat r and z = Ahat s).  The float sweeps stage their matrix
+//           slices in shared memory with bulk copies when it fits.
 #include <cuda_runtime.h>
 
 #include <algorithm>
