@@ -27,6 +27,7 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr uint32_t kLowerBit = 0x80000000u;
 constexpr uint32_t kPadFid = 0xffffffffu;
 constexpr int kMetaSmemMax = 32 * 1024;   // dynamic shared memory for slice metadata
+constexpr int kDefaultMinSlices = 8;      // ldu_opts.min_slices when 0
 
 // error bits raised by device-side validation
 enum : int {
@@ -99,6 +100,7 @@ struct ldu_matrix {
     int block_threads;
     int blocks_per_sm;
     int staging;               // 0 auto, -1 off
+    int min_slices;            // at most one block per min_slices slices (<= 0: no limit)
     int64_t device_bytes;
     // structure
     int *slice_ptr, *slice_w, *col;
@@ -128,9 +130,9 @@ ldu::SellView view_of(const ldu_matrix *A);
 int cuda_status(cudaError_t e);
 int launch_persistent(const void *kernel, int grid, int block, void **args, size_t smem,
                       cudaStream_t s);
-int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid, size_t *smem);
 int grid_for_smem(const ldu_matrix *A, const void *kernel, int block, size_t smem, int *grid);
-int meta_smem_bytes(int64_t n_slices, int num_sms, size_t *bytes);
+int meta_smem_bytes(int64_t n_slices, int blocks, size_t *bytes);
+int grid_cap(const ldu_matrix *A);
 
 // ---------------------------------------------------------------------------
 // device helpers

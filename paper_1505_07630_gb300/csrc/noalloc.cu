@@ -201,13 +201,17 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     CK(cudaGetLastError());
 
     const void *kern = (const void *)k_pcg64<4, Batch<4>::pcg>;   // pcg_solve's kernel for C = 128
+    // the launch shape of a default handle: at most one block per
+    // kDefaultMinSlices slices, metadata sized for the resulting share
+    const int64_t cap = std::max<int64_t>(1, n_slices / kDefaultMinSlices);
     size_t smem = 0;
-    meta_smem_bytes(n_slices, sms, &smem);
+    meta_smem_bytes(n_slices, (int)std::min<int64_t>(sms, cap), &smem);
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNoallocBlock, smem));
     if (per_sm < 1)
         return LDU_ERR_UNSUPPORTED;
-    const int grid = (int)std::min<int64_t>({(int64_t)per_sm * sms, (int64_t)sms * 32, kMaxGrid});
+    const int grid =
+        (int)std::min<int64_t>({(int64_t)per_sm * sms, (int64_t)sms * 32, kMaxGrid, cap});
 
     SolveParams P;
     P.A.n = (int)n;

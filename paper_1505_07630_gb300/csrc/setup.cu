@@ -48,30 +48,21 @@ SellView view_of(const ldu_matrix *A) {
     return v;
 }
 
-// Shared memory for the per-block slice metadata: enough for the largest
-// block share at one block per SM; 0 (global reads) above kMetaSmemMax, so
-// that with the kernels' static shared memory a block stays within the
-// default 48 KB.
-int meta_smem_bytes(int64_t n_slices, int num_sms, size_t *bytes) {
-    const int64_t per_block = (n_slices + num_sms - 1) / num_sms;
-    const int64_t b = per_block * (int64_t)sizeof(int2);
-    *bytes = b <= kMetaSmemMax ? (size_t)b : 0;
-    return LDU_OK;
+// Largest grid of a single-system launch: one block per min_slices slices.
+int grid_cap(const ldu_matrix *A) {
+    if (A->min_slices <= 0 || A->batch)
+        return 1 << 30;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(A->n_slices / A->min_slices, 1 << 30));
 }
 
-int grid_for(const ldu_matrix *A, const void *kernel, int block, int *grid, size_t *smem) {
-    meta_smem_bytes(A->n_slices, A->num_sms, smem);
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, *smem);
-    if (e != cudaSuccess)
-        return cuda_status(e);
-    if (per_sm < 1)
-        return LDU_ERR_UNSUPPORTED;
-    if (A->blocks_per_sm > 0)
-        per_sm = std::min(per_sm, A->blocks_per_sm);
-    int g = per_sm * A->num_sms;
-    g = std::min(g, A->max_grid);
-    *grid = g;
+// Shared memory for the per-block slice metadata: enough for the largest
+// block share when the grid has at least `blocks` blocks; 0 (global reads)
+// above kMetaSmemMax, so that with the kernels' static shared memory a
+// block stays within the default 48 KB.
+int meta_smem_bytes(int64_t n_slices, int blocks, size_t *bytes) {
+    const int64_t per_block = (n_slices + blocks - 1) / blocks;
+    const int64_t b = per_block * (int64_t)sizeof(int2);
+    *bytes = b <= kMetaSmemMax ? (size_t)b : 0;
     return LDU_OK;
 }
 
@@ -93,6 +84,7 @@ int grid_for_smem(const ldu_matrix *A, const void *kernel, int block, size_t sme
     if (A->blocks_per_sm > 0)
         per_sm = std::min(per_sm, A->blocks_per_sm);
     *grid = std::min(per_sm * A->num_sms, A->max_grid);
+    *grid = std::min(*grid, grid_cap(A));
     return LDU_OK;
 }
 
@@ -190,7 +182,7 @@ int ldu_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *neigh
     *out = nullptr;
     if (n < 0 || nf < 0 || (n > 0 && !diag) || (nf > 0 && (!owner || !neighbour || !upper || !lower)))
         return LDU_ERR_BAD_ARG;
-    int C = 128, bt = 256, bps = 0, stg = 0;
+    int C = 128, bt = 256, bps = 0, stg = 0, msl = kDefaultMinSlices;
     if (opt) {
         if (opt->slice_rows)
             C = opt->slice_rows;
@@ -198,9 +190,11 @@ int ldu_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *neigh
             bt = opt->block_threads;
         bps = opt->blocks_per_sm;
         stg = opt->staging;
+        if (opt->min_slices)
+            msl = opt->min_slices;
     }
     if ((C != 32 && C != 64 && C != 128) || (bt != 128 && bt != 256) || bps < 0 ||
-        (stg != 0 && stg != -1))
+        (stg != 0 && stg != -1) || msl < -1)
         return LDU_ERR_BAD_ARG;
     if (n >= (int64_t)1 << 31 || nf >= (int64_t)1 << 30)
         return LDU_ERR_UNSUPPORTED;
@@ -231,6 +225,7 @@ int ldu_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *neigh
     A->block_threads = bt;
     A->blocks_per_sm = bps;
     A->staging = stg;
+    A->min_slices = msl;
     A->n_slices = (n + C - 1) / C;
     A->n_pad = A->n_slices * C;
     A->max_grid = A->num_sms * 32;

@@ -149,7 +149,8 @@ int run_solver(const ldu_matrix *Ac, Kind kind, const double *b, double *x, doub
     }
     const Kind kk = (kind == kMixed && opt.deflate) ? kMixedDeflated : kind;
     size_t meta = 0;
-    meta_smem_bytes(A->n_slices, A->num_sms, &meta);
+    // the grid has at least min(SMs, cap) blocks: size the metadata for that
+    meta_smem_bytes(A->n_slices, std::min(A->num_sms, grid_cap(A)), &meta);
     const int meta_cap = (int)(meta / sizeof(int2));
     size_t smem = meta;
     const int minb = mixed_minb(A->C / 32, A->blocks_per_sm);

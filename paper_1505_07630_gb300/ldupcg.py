@@ -29,7 +29,8 @@ class LduError(RuntimeError):
 
 class LduOpts(ctypes.Structure):
     _fields_ = [("slice_rows", ctypes.c_int), ("block_threads", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("staging", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("staging", ctypes.c_int),
+                ("min_slices", ctypes.c_int)]
 
 
 class PcgOpts(ctypes.Structure):
@@ -186,14 +187,14 @@ class LduMatrix:
 
 
 def ldu_create(n, owner, neighbour, diag, upper, lower, slice_rows=0, block_threads=0,
-               blocks_per_sm=0, staging=0, stream=None):
+               blocks_per_sm=0, staging=0, min_slices=0, stream=None):
     """Create a handle from device tensors (int32 owner/neighbour, float64 values)."""
     nf = owner.numel()
     args = [ctypes.c_int64(n), ctypes.c_int64(nf),
             _dev(owner, torch.int32, nf, "owner"), _dev(neighbour, torch.int32, nf, "neighbour"),
             _dev(diag, torch.float64, n, "diag"), _dev(upper, torch.float64, nf, "upper"),
             _dev(lower, torch.float64, nf, "lower")]
-    opts = LduOpts(slice_rows, block_threads, blocks_per_sm, staging)
+    opts = LduOpts(slice_rows, block_threads, blocks_per_sm, staging, min_slices)
     h = _vp()
     st = lib().ldu_create(*args, ctypes.byref(opts), _stream(stream), ctypes.byref(h))
     _check(st, "ldu_create", allow_not_converged=False)
@@ -315,7 +316,8 @@ def from_system(sys_, device="cuda", **opts):
 # ---- batches ----------------------------------------------------------------
 
 def ldu_create_batched(sizes, face_counts, owner, neighbour, diag, upper, lower, slice_rows=0,
-                       block_threads=0, blocks_per_sm=0, staging=0, stream=None):
+                       block_threads=0, blocks_per_sm=0, staging=0, min_slices=0,
+                       stream=None):
     """Batched handle from concatenated device arrays (face indices local to
     their system).  sizes / face_counts: per-system cells and faces."""
     import numpy as np
@@ -323,7 +325,7 @@ def ldu_create_batched(sizes, face_counts, owner, neighbour, diag, upper, lower,
     n_h = np.ascontiguousarray(sizes, dtype=np.int64)
     f_h = np.ascontiguousarray(face_counts, dtype=np.int64)
     n_tot, f_tot = int(n_h.sum()), int(f_h.sum())
-    opts = LduOpts(slice_rows, block_threads, blocks_per_sm, staging)
+    opts = LduOpts(slice_rows, block_threads, blocks_per_sm, staging, min_slices)
     h = _vp()
     st = lib().ldu_create_batched(
         nsys, _vp(n_h.ctypes.data), _vp(f_h.ctypes.data), _dev(owner, torch.int32, f_tot, "owner"),

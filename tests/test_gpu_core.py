@@ -267,8 +267,10 @@ def test_not_spd_and_bad_addressing(pkg):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_barrier_timeout_is_reported_and_recoverable(pkg, oracle_mod, precision):
+    """Block 0 leaves before its first barrier; the others time out.  The
+    block limit is lifted so that this small system still has other blocks."""
     s = lc.config1(s=10)
-    A = pkg.from_system(s)
+    A = pkg.from_system(s, min_slices=-1)
     _, st, _, _ = pkg.pipecg_solve(A, cuda(s.b), precision=precision, barrier_timeout_s=0.2,
                                    fault_inject=1, check=False)
     assert st == pkg.ldupcg.ERR_BARRIER_TIMEOUT
@@ -365,3 +367,27 @@ def test_col16_offsets_at_the_int16_limit(pkg, oracle_mod, ny, fits):
     B = pkg.from_system(s, slice_rows=64, staging=-1)
     assert B.info()["col16"] == 0          # plain loads never read them
     B.close()
+
+
+@pytest.mark.parametrize("solver", ["pcg", "mixed"])
+def test_small_systems_use_fewer_blocks(pkg, oracle_mod, solver):
+    """By default a single-system launch gives each block at least 8 slices:
+    a 16^3 system (32 slices of 128 rows) runs on 4 blocks, and the same
+    solve without the limit (one block per resident slot, most of them
+    idle) reaches the same solution."""
+    s = lc.config1(s=16)
+    b = cuda(s.b)
+    out = {}
+    for ms in (0, -1):
+        A = pkg.from_system(s, min_slices=ms)
+        if solver == "pcg":
+            x, st, it, rr = pkg.pcg_solve(A, b, tol=1e-10)
+        else:
+            x, st, it, rr = pkg.pipecg_solve(A, b, tol=1e-10, precision="mixed")
+        assert st == 0 and oracle_mod.true_relres(s, x.cpu().numpy()) <= 1.01e-10
+        out[ms] = (x.cpu().numpy(), it, A.stats()["grid_blocks"])
+        A.close()
+    assert out[0][2] == 4
+    assert out[-1][2] > 4
+    assert abs(out[0][1] - out[-1][1]) <= 2
+    assert np.linalg.norm(out[0][0] - out[-1][0]) <= 1e-8 * np.linalg.norm(out[-1][0])
