@@ -21,7 +21,7 @@ import numpy as np
 
 from . import rng
 from .mesh import (BoxGeometry, assemble, diffusion_coefficients, flux_divergence,
-                   graded_widths, pressure_coefficients, uniform_widths)
+                   graded_widths, harmonic_factors, pressure_coefficients, uniform_widths)
 from .reorder import random_order, rcm_order, renumber
 
 X_WALLS = ((0, 0), (0, 1))
@@ -54,6 +54,7 @@ def poisson_box(nx, ny=None, nz=None, seed=0, sub=0, diffusivity="unit", sigma=1
     s = assemble(geo, coef, extra, b, name=name,
                  meta=dict(seed=seed, sub=sub, diffusivity=diffusivity, dirichlet=dirichlet))
     s.meta["k_cell"] = k
+    s.meta["g_face"], s.meta["bfac"] = harmonic_factors(geo, dirichlet)
     return s
 
 

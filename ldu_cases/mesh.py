@@ -155,6 +155,21 @@ def diffusion_coefficients(geo, k_cell, dirichlet_axes=((0, 0), (0, 1))):
     return coef, extra
 
 
+def harmonic_factors(geo, dirichlet_axes=((0, 0), (0, 1))):
+    """The geometry of diffusion_coefficients without the diffusivity:
+    g_f = |S_f| / |d_PN| per internal face and bfac_P = sum over the
+    Dirichlet walls of cell P of 2 |S_b| / w_P, so that for any cell
+    diffusivity k the face coefficients are g_f * 2 k_P k_N / (k_P + k_N) and
+    the boundary diagonal terms k_P * bfac_P."""
+    area, dP, dN = geo.internal_face_geometry()
+    g = area / (dP + dN)
+    bfac = np.zeros(geo.n)
+    for axis, side in dirichlet_axes:
+        cells = geo.wall_cells(axis, side)
+        bfac[cells] += 2.0 * geo.face_area(cells, axis) / geo.cell_width(cells, axis)
+    return g, bfac
+
+
 def pressure_coefficients(geo, aP):
     """icoFoam-style pressure coefficients c_f = |S_f| / |d_PN| * (1/a)_f with
     1/a interpolated linearly to the face, weight d_N/(d_P+d_N) on the owner."""

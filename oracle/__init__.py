@@ -5,7 +5,8 @@ benchmark's CPU-baseline leg, never by the library.  It shares no code with
 the CUDA path; the two meet only in the seeded inputs of `ldu_cases`.
 
 Routines (C source in ldu_oracle.c, each citing what it restates):
-  spmv, pcg, pipecg, mixed_pipecg, face_grad, lu_solve, true_relres
+  spmv, pcg, pipecg, mixed_pipecg, face_grad, harmonic_coeffs, harmonic_grad,
+  lu_solve, true_relres
 plus two plain numpy helpers, `dense` (the LDU matrix written out densely)
 and `matrix_from_coef` (the FVM matrix of a set of face coefficients).
 """
@@ -43,6 +44,10 @@ def lib():
         L.or_mixed_pipecg.restype = c_int
         L.or_face_grad.argtypes = [i64, _i32, _i32, _d, _d, _d]
         L.or_face_grad.restype = None
+        L.or_harmonic_coeffs.argtypes = [i64, i64, _i32, _i32, _d, _d, _d, _d, _d]
+        L.or_harmonic_coeffs.restype = None
+        L.or_harmonic_grad.argtypes = [i64, i64, _i32, _i32, _d, _d, _d, _d, _d, _d]
+        L.or_harmonic_grad.restype = None
         L.or_lu_solve.argtypes = [i64, _d, _d]
         L.or_lu_solve.restype = c_int
     return _lib
@@ -146,6 +151,31 @@ def face_grad(owner, neighbour, lam, x):
     lib().or_face_grad(ctypes.c_int64(ow.shape[0]), _p(ow, _i32), _p(nb, _i32), _p(lam), _p(x),
                        _p(g))
     return g
+
+
+def harmonic_coeffs(owner, neighbour, k, g, bfac):
+    """(coef, extra): c_f = g_f 2 k_o k_n / (k_o + k_n), extra_P = k_P bfac_P."""
+    ow = np.ascontiguousarray(owner, dtype=np.int32)
+    nb = np.ascontiguousarray(neighbour, dtype=np.int32)
+    k, g, bfac = _f64(k), _f64(g), _f64(bfac)
+    coef = np.empty(ow.shape[0])
+    extra = np.empty(k.shape[0])
+    lib().or_harmonic_coeffs(ctypes.c_int64(k.shape[0]), ctypes.c_int64(ow.shape[0]),
+                             _p(ow, _i32), _p(nb, _i32), _p(k), _p(g), _p(bfac), _p(coef),
+                             _p(extra))
+    return coef, extra
+
+
+def harmonic_grad(owner, neighbour, k, g, bfac, dcoef, dextra):
+    """dL/dk per cell from dL/dcoef and dL/dextra (chain rule of harmonic_coeffs)."""
+    ow = np.ascontiguousarray(owner, dtype=np.int32)
+    nb = np.ascontiguousarray(neighbour, dtype=np.int32)
+    k, g, bfac, dcoef, dextra = _f64(k), _f64(g), _f64(bfac), _f64(dcoef), _f64(dextra)
+    dk = np.empty(k.shape[0])
+    lib().or_harmonic_grad(ctypes.c_int64(k.shape[0]), ctypes.c_int64(ow.shape[0]),
+                           _p(ow, _i32), _p(nb, _i32), _p(k), _p(g), _p(bfac), _p(dcoef),
+                           _p(dextra), _p(dk))
+    return dk
 
 
 def lu_solve(A, b):

@@ -16,6 +16,9 @@
  *   or_mixed_pipecg   FP32 pipelined PCG with FP64 residual replacement and FP64
  *                     solution accumulation (reliable updates or defect correction)
  *   or_face_grad      adjoint face-coefficient gradient -(l_o - l_n)(x_o - x_n)
+ *   or_harmonic_coeffs / or_harmonic_grad
+ *                     face coefficients from cell diffusivities through the
+ *                     harmonic mean, and the chain rule back to the cells
  *   or_lu_solve       dense LU with partial pivoting (tiny systems)
  *
  * Conventions shared with the library's interface (not its code): upper[f]
@@ -577,6 +580,43 @@ void or_face_grad(int64_t nf, const int32_t *own, const int32_t *nbr,
 {
     for (int64_t f = 0; f < nf; f++)
         grad[f] = -(lambda[own[f]] - lambda[nbr[f]]) * (x[own[f]] - x[nbr[f]]);
+}
+
+/* ---- cell diffusivity -> face coefficients (harmonic mean) -----------------
+ * The FVM Laplacian's face coefficient is c_f = g_f k_f with the harmonic
+ * mean k_f = 2 k_o k_n / (k_o + k_n) of the two cells' diffusivities and a
+ * geometric factor g_f = |S_f| / |d_on|; a Dirichlet wall adds k_P bfac_P to
+ * the diagonal of its cell (bfac_P = 2 |S_b| / w_P summed over the cell's
+ * Dirichlet faces). */
+void or_harmonic_coeffs(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
+                        const double *k, const double *g, const double *bfac,
+                        double *coef, double *extra)
+{
+    for (int64_t f = 0; f < nf; f++) {
+        double ko = k[own[f]], kn = k[nbr[f]];
+        coef[f] = g[f] * (2.0 * ko * kn / (ko + kn));
+    }
+    for (int64_t i = 0; i < n; i++)
+        extra[i] = k[i] * bfac[i];
+}
+
+/* Chain rule of the map above: given dL/dc_f and dL/dextra_P,
+ *   dL/dk_P = sum over the faces f of P of dL/dc_f g_f dk_f/dk_P
+ *             + dL/dextra_P bfac_P,
+ * with dk_f/dk_o = 2 k_n^2 / (k_o + k_n)^2 (and symmetrically for n).
+ * Face loop, each face adding to both of its cells. */
+void or_harmonic_grad(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
+                      const double *k, const double *g, const double *bfac,
+                      const double *dcoef, const double *dextra, double *dk)
+{
+    for (int64_t i = 0; i < n; i++)
+        dk[i] = dextra[i] * bfac[i];
+    for (int64_t f = 0; f < nf; f++) {
+        double ko = k[own[f]], kn = k[nbr[f]], s = ko + kn;
+        double w = dcoef[f] * g[f] * 2.0 / (s * s);
+        dk[own[f]] += w * kn * kn;
+        dk[nbr[f]] += w * ko * ko;
+    }
 }
 
 /* ---- dense LU with partial pivoting (row-major, n x n, A and b overwritten;

@@ -292,6 +292,53 @@ def test_face_gradient_matches_finite_differences(oracle_mod):
     assert np.max(np.abs(fd_b - lam)) <= 1e-5 * np.max(np.abs(lam))
 
 
+def test_harmonic_coeffs_match_the_assembly(oracle_mod):
+    """The oracle's map from cell diffusivities to face coefficients and
+    wall terms reproduces the generator's assembly of the same box."""
+    s = lc.poisson_box(6, 5, 4, diffusivity="lognormal", seed=11)
+    coef, extra = oracle_mod.harmonic_coeffs(s.owner, s.neighbour, s.meta["k_cell"],
+                                             s.meta["g_face"], s.meta["bfac"])
+    assert np.allclose(coef, s.coef, rtol=1e-15, atol=0)
+    assert np.allclose(extra, s.diag_extra, rtol=1e-15, atol=0)
+    assert np.all(extra[s.diag_extra == 0] == 0)
+
+
+def test_cell_diffusivity_gradient_matches_finite_differences(oracle_mod):
+    """dL/dk_P through the harmonic-mean faces and the Dirichlet wall terms
+    (adjoint solve, face gradient, chain rule) against central differences
+    of L(k) = 0.5 ||x(k) - x_t||^2 with x(k) from a dense LU solve."""
+    s = lc.poisson_box(3, 4, 3, diffusivity="lognormal", seed=12)
+    k0, gf, bfac = s.meta["k_cell"], s.meta["g_face"], s.meta["bfac"]
+    x_t = np.random.default_rng(3).uniform(-1, 1, s.n)
+
+    def solve(k):
+        coef, extra = oracle_mod.harmonic_coeffs(s.owner, s.neighbour, k, gf, bfac)
+        diag = extra.copy()
+        np.add.at(diag, s.owner, coef)
+        np.add.at(diag, s.neighbour, coef)
+        M = oracle_mod.dense(s, diag, -coef, -coef)
+        return M, oracle_mod.lu_solve(M, s.b)
+
+    M, x = solve(k0)
+    lam = oracle_mod.lu_solve(M.T, x - x_t)
+    dcoef = oracle_mod.face_grad(s.owner, s.neighbour, lam, x)
+    dk = oracle_mod.harmonic_grad(s.owner, s.neighbour, k0, gf, bfac, dcoef, -lam * x)
+    fd = np.empty(s.n)
+    for i in range(s.n):
+        h = 1e-6 * k0[i]
+        kp, km = k0.copy(), k0.copy()
+        kp[i] += h
+        km[i] -= h
+        xp, xm = solve(kp)[1], solve(km)[1]
+        fd[i] = 0.5 * np.sum((xp - xm) * (xp + xm - 2 * x_t)) / (2 * h)
+    assert np.max(np.abs(fd - dk)) <= 1e-5 * np.max(np.abs(dk))
+    # a wall cell's derivative includes its wall term: dropping it is visible
+    wall = np.flatnonzero(bfac > 0)
+    no_wall = oracle_mod.harmonic_grad(s.owner, s.neighbour, k0, gf, np.zeros(s.n), dcoef,
+                                       -lam * x)
+    assert np.max(np.abs(no_wall[wall] - fd[wall])) > 1e-3 * np.max(np.abs(dk))
+
+
 # ---- Table 2 magnitudes (soft) ---------------------------------------------------
 
 def test_table2_plain_cg_magnitude(oracle_mod):
