@@ -565,7 +565,8 @@ def run_autograd(args, dev, pkg, timed_fn):
     """Differentiable solve on a 64³ mesh, batch of 8 diffusivity fields:
     loss 0.5 ||x(c) - x_t||², forward solve plus backward (adjoint solve and
     face/diagonal/RHS gradients) in one batched handle, mixed precision to
-    1e-10; targets from FP64 solves of the reference fields."""
+    1e-10; targets from FP64 solves of the reference fields.  Timed again
+    with the cell diffusivities as the parameters."""
     import numpy as np
     import torch
 
@@ -590,9 +591,24 @@ def run_autograd(args, dev, pkg, timed_fn):
         return c.grad
 
     t = timed_fn(step, 2, 1)
+    # the same loss as a function of every cell's diffusivity (harmonic-mean
+    # faces and wall terms in the library's kernels)
+    kc = torch.as_tensor(np.concatenate([q.meta["k_cell"] for q in systems]), device=dev)
+    gf = torch.as_tensor(np.concatenate([q.meta["g_face"] for q in systems]), device=dev)
+    bf = torch.as_tensor(np.concatenate([q.meta["bfac"] for q in systems]), device=dev)
+
+    def step_k():
+        kk = kc.clone().requires_grad_(True)
+        c, e = pkg.harmonic_coeffs(A, kk, gf, bf)
+        xs = pkg.ldu_solve(A, c, e, b, precision="mixed", tol=1e-10)
+        (0.5 * ((xs - xt) ** 2).sum()).backward()
+        return kk.grad
+
+    t_k = timed_fn(step_k, 2, 1)
     A.close()
     return {"systems": len(systems), "cells_each": systems[0].n,
-            "faces_each": systems[0].nfaces, "forward_backward_s": statistics.median(t)}
+            "faces_each": systems[0].nfaces, "forward_backward_s": statistics.median(t),
+            "forward_backward_cell_k_s": statistics.median(t_k)}
 
 
 def main():

@@ -224,6 +224,33 @@ int ldu_face_grad(const ldu_matrix *A, const double *lambda, const double *x, do
 int ldu_diag_grad(const ldu_matrix *A, const double *lambda, const double *x, double *ddiag,
                   ldu_stream_t stream);
 
+/* Face coefficients and wall terms of the FVM Laplacian from cell
+ * diffusivities (Eq. 8's laplacian operator, discretised as in Sec. 5's
+ * lduMatrix): with the harmonic mean k_f = 2 k_o k_n / (k_o + k_n) of the
+ * two cells of face f,
+ *   coef[f]       = g[f] * k_f           (pass to ldu_set_face_coeffs)
+ *   diag_extra[i] = k[i] * bfac[i]       (Dirichlet-wall part of the diagonal)
+ *   k           device double[cells], every entry > 0
+ *   g           device double[nFaces]: geometric factor |S_f| / |d_on| of each face
+ *   bfac        device double[cells]: sum of 2 |S_b| / w_P over the cell's Dirichlet faces
+ *   coef, diag_extra   device double[nFaces] / [cells] outputs
+ * All arrays in the caller's face and cell order (concatenated for a batched
+ * handle).  Queued on stream. */
+int ldu_harmonic_coeffs(const ldu_matrix *A, const double *k, const double *g,
+                        const double *bfac, double *coef, double *diag_extra,
+                        ldu_stream_t stream);
+
+/* Chain rule of ldu_harmonic_coeffs: from dL/dcoef and dL/ddiag_extra (for
+ * instance ldu_face_grad's and ldu_diag_grad's outputs),
+ *   dk[P] = ddiag_extra[P] * bfac[P]
+ *         + sum over the faces f of P of dcoef[f] * g[f] * 2 k_N^2 / (k_P + k_N)^2
+ * where N is the other cell of f.  Each cell's sum is formed in a fixed order
+ * (no atomics), so repeated calls agree bitwise.  Arguments as
+ * ldu_harmonic_coeffs; dk: device double[cells].  Queued on stream. */
+int ldu_harmonic_grad(const ldu_matrix *A, const double *k, const double *g, const double *bfac,
+                      const double *dcoef, const double *ddiag_extra, double *dk,
+                      ldu_stream_t stream);
+
 /* Counters of the last solve (host struct filled from host memory; no sync). */
 int ldu_last_stats(const ldu_matrix *A, ldu_solve_stats *stats);
 

@@ -10,6 +10,13 @@ solve, and
     dL/d(diag_extra)_i = -lambda_i x_i               (ldu_diag_grad)
 The handle may be a batched handle: b, x, c and diag_extra are then the
 systems' arrays concatenated, and both solves are one batched launch.
+
+harmonic_coeffs maps cell diffusivities k to (c, diag_extra) through the
+harmonic-mean faces of the FVM Laplacian (ldu_harmonic_coeffs), with
+    dL/dk_P = dL/d(diag_extra)_P bfac_P
+              + sum over the faces f of P of dL/dc_f g_f 2 k_N^2 / (k_P + k_N)^2
+in the library's kernel (ldu_harmonic_grad); composed with ldu_solve it
+gives the gradient of a loss with respect to every cell's diffusivity.
 """
 import torch
 
@@ -66,3 +73,32 @@ def ldu_solve(A, coef, diag_extra, b, precision="fp64", tol=1e-12, maxit=100000,
     precision: 'fp64' (Jacobi-PCG), 'pipe' (FP64 pipelined) or 'mixed'."""
     cfg = dict(precision=precision, tol=tol, maxit=maxit, x0=x0, check=check, kw=kw)
     return LduSolve.apply(coef, diag_extra, b, A, cfg)
+
+
+class HarmonicCoeffs(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, k, g, bfac, A):
+        k = k.detach().contiguous()
+        g = g.detach().contiguous()
+        bfac = bfac.detach().contiguous()
+        coef, extra = ldupcg.ldu_harmonic_coeffs(A, k, g, bfac)
+        ctx.save_for_backward(k, g, bfac)
+        ctx.A = A
+        return coef, extra
+
+    @staticmethod
+    def backward(ctx, g_coef, g_extra):
+        k, g, bfac = ctx.saved_tensors
+        if g_coef is None:
+            g_coef = torch.zeros(ctx.A.nfaces, dtype=torch.float64, device=k.device)
+        if g_extra is None:
+            g_extra = torch.zeros_like(k)
+        dk = ldupcg.ldu_harmonic_grad(ctx.A, k, g, bfac, g_coef.contiguous(),
+                                      g_extra.contiguous())
+        return dk, None, None, None
+
+
+def harmonic_coeffs(A, k, g, bfac):
+    """(coef, diag_extra) of cell diffusivities k, differentiable in k.
+    g: geometric factor per internal face; bfac: Dirichlet-wall factor per cell."""
+    return HarmonicCoeffs.apply(k, g, bfac, A)

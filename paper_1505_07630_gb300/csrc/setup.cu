@@ -436,6 +436,34 @@ int ldu_face_grad(const ldu_matrix *A, const double *lambda, const double *x, do
     return cuda_status(cudaGetLastError());
 }
 
+int ldu_harmonic_coeffs(const ldu_matrix *A, const double *k, const double *g,
+                        const double *bfac, double *coef, double *diag_extra,
+                        ldu_stream_t stream) {
+    if (!A || (A->n_cells > 0 && (!k || !bfac || !diag_extra)) ||
+        (A->nf > 0 && (!g || !coef)))
+        return LDU_ERR_BAD_ARG;
+    if (A->nf == 0 && A->n_cells == 0)
+        return LDU_OK;
+    k_harmonic_coeffs<<<blocks_for(std::max(A->nf, A->n_cells), 256), 256, 0,
+                        (cudaStream_t)stream>>>(A->nf, A->n_cells, A->owner, A->neighbour, k, g,
+                                                bfac, coef, diag_extra);
+    return cuda_status(cudaGetLastError());
+}
+
+int ldu_harmonic_grad(const ldu_matrix *A, const double *k, const double *g, const double *bfac,
+                      const double *dcoef, const double *ddiag_extra, double *dk,
+                      ldu_stream_t stream) {
+    if (!A || (A->n_cells > 0 && (!k || !bfac || !ddiag_extra || !dk)) ||
+        (A->nf > 0 && (!g || !dcoef)))
+        return LDU_ERR_BAD_ARG;
+    if (A->n_pad == 0)
+        return LDU_OK;
+    k_harmonic_grad<<<blocks_for(A->n_pad, 256), 256, 0, (cudaStream_t)stream>>>(
+        (int)A->n_pad, (int)A->n, A->C, A->slice_ptr, A->slice_w, A->col, A->fid, A->row_cell, k,
+        g, bfac, dcoef, ddiag_extra, dk);
+    return cuda_status(cudaGetLastError());
+}
+
 int ldu_diag_grad(const ldu_matrix *A, const double *lambda, const double *x, double *ddiag,
                   ldu_stream_t stream) {
     if (!A || (A->n_cells > 0 && (!lambda || !x || !ddiag)))

@@ -249,6 +249,55 @@ __global__ void k_diag_grad(int64_t n, const double *__restrict__ lam,
         g[i] = -lam[i] * x[i];
 }
 
+// cell diffusivity -> face coefficients (harmonic mean) and wall terms;
+// owner/neighbour and k in the caller's cell numbering
+__global__ void k_harmonic_coeffs(int64_t nf, int64_t n, const int32_t *__restrict__ own,
+                                  const int32_t *__restrict__ nbr, const double *__restrict__ k,
+                                  const double *__restrict__ g, const double *__restrict__ bfac,
+                                  double *__restrict__ coef, double *__restrict__ extra) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += stride) {
+        const double ko = k[own[f]], kn = k[nbr[f]];
+        coef[f] = g[f] * (2.0 * ko * kn / (ko + kn));
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+        extra[i] = k[i] * bfac[i];
+}
+
+// dL/dk of the cell of row r: its wall term plus, over the faces of its
+// stored slots in slot order, dL/dc_f g_f dk_f/dk_P with
+// dk_f/dk_P = 2 k_N^2 / (k_P + k_N)^2.  One thread per row, no atomics.
+// row_cell (batched handles) maps rows to caller cells, -1 between systems;
+// without it rows below n are cells.
+__global__ void k_harmonic_grad(int n_pad, int n, int C, const int *slice_ptr, const int *slice_w,
+                                const int *col, const uint32_t *fid, const int *row_cell,
+                                const double *__restrict__ k, const double *__restrict__ g,
+                                const double *__restrict__ bfac, const double *__restrict__ dcoef,
+                                const double *__restrict__ dextra, double *__restrict__ dk) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_pad)
+        return;
+    const int cell = row_cell ? row_cell[r] : (r < n ? r : -1);
+    if (cell < 0)
+        return;
+    const int s = r / C, i = r - s * C;
+    const int base = slice_ptr[s] + i, w = slice_w[s];
+    const double kp = k[cell];
+    double acc = dextra[cell] * bfac[cell];
+    for (int q = 0; q < w; ++q) {
+        const int at = base + q * C;
+        const uint32_t f = fid[at];
+        if (f == kPadFid)
+            continue;
+        const uint32_t face = f & ~kLowerBit;
+        const int nrow = col[at];
+        const double kn = k[row_cell ? row_cell[nrow] : nrow];
+        const double sum = kp + kn;
+        acc += dcoef[face] * g[face] * (2.0 * kn * kn / (sum * sum));
+    }
+    dk[cell] = acc;
+}
+
 __global__ void k_face_grad(int64_t nf, const int32_t *__restrict__ own,
                             const int32_t *__restrict__ nbr, const double *__restrict__ lam,
                             const double *__restrict__ x, double *__restrict__ g) {

@@ -92,6 +92,10 @@ def lib():
         L.ldu_face_grad.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.ldu_diag_grad.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.ldu_diag_grad.restype = i
+        L.ldu_harmonic_coeffs.argtypes = [_vp] * 7
+        L.ldu_harmonic_coeffs.restype = i
+        L.ldu_harmonic_grad.argtypes = [_vp] * 8
+        L.ldu_harmonic_grad.restype = i
         L.ldu_last_stats.argtypes = [_vp, ctypes.POINTER(LduSolveStats)]
         L.ldu_get_info.argtypes = [_vp, ctypes.POINTER(LduInfo)]
         L.ldu_destroy.argtypes = [_vp]
@@ -297,6 +301,37 @@ def ldu_diag_grad(A, lam, x, out=None, stream=None):
                              _dev(x, torch.float64, A.n, "x"),
                              _dev(out, torch.float64, A.n, "ddiag"), _stream(stream))
     _check(st, "ldu_diag_grad", allow_not_converged=False)
+    return out
+
+
+def ldu_harmonic_coeffs(A, k, g, bfac, coef=None, extra=None, stream=None):
+    """(coef, diag_extra) of the FVM Laplacian for cell diffusivities k:
+    coef_f = g_f 2 k_o k_n / (k_o + k_n), diag_extra_P = k_P bfac_P."""
+    if coef is None:
+        coef = torch.empty(A.nfaces, dtype=torch.float64, device=k.device)
+    if extra is None:
+        extra = torch.empty(A.n, dtype=torch.float64, device=k.device)
+    st = lib().ldu_harmonic_coeffs(A.handle, _dev(k, torch.float64, A.n, "k"),
+                                   _dev(g, torch.float64, A.nfaces, "g"),
+                                   _dev(bfac, torch.float64, A.n, "bfac"),
+                                   _dev(coef, torch.float64, A.nfaces, "coef"),
+                                   _dev(extra, torch.float64, A.n, "diag_extra"), _stream(stream))
+    _check(st, "ldu_harmonic_coeffs", allow_not_converged=False)
+    return coef, extra
+
+
+def ldu_harmonic_grad(A, k, g, bfac, dcoef, dextra, out=None, stream=None):
+    """dL/dk from dL/dcoef and dL/d(diag_extra) (chain rule of
+    ldu_harmonic_coeffs), one fixed-order sum per cell."""
+    if out is None:
+        out = torch.empty(A.n, dtype=torch.float64, device=k.device)
+    st = lib().ldu_harmonic_grad(A.handle, _dev(k, torch.float64, A.n, "k"),
+                                 _dev(g, torch.float64, A.nfaces, "g"),
+                                 _dev(bfac, torch.float64, A.n, "bfac"),
+                                 _dev(dcoef, torch.float64, A.nfaces, "dcoef"),
+                                 _dev(dextra, torch.float64, A.n, "ddiag_extra"),
+                                 _dev(out, torch.float64, A.n, "dk"), _stream(stream))
+    _check(st, "ldu_harmonic_grad", allow_not_converged=False)
     return out
 
 
