@@ -423,10 +423,11 @@ def run_ours(args):
     batched = None
     if not args.skip_batched:
         batched = run_batched(args, dev, pkg, timed_fn=timed_generic)
-    pressure = autograd_case = None
+    pressure = autograd_case = heat = None
     if not args.skip_extra:
         pressure = run_pressure(args, dev, pkg, timed_fn=timed_generic)
         autograd_case = run_autograd(args, dev, pkg, timed_fn=timed_generic)
+        heat = run_heat(args, dev, pkg, timed_fn=timed_generic)
 
     # CPU baseline: the oracle on this host, bounded sample, rank 0 only
     cpu = None
@@ -469,6 +470,7 @@ def run_ours(args):
         "batched": batched,
         "pressure256": pressure,
         "differentiable": autograd_case,
+        "heat_steps": heat,
     }
     line.update(extra)
     emit(line, ranks)
@@ -559,6 +561,44 @@ def run_pressure(args, dev, pkg, timed_fn):
     out["speedup_mixed_vs_fp64_pcg"] = out["fp64_pcg"]["s"] / out["mixed_deflated"]["s"]
     A.close()
     return out
+
+
+def run_heat(args, dev, pkg, timed_fn):
+    """laplacianFoam-style transient: 10 backward-Euler steps of the 128³
+    lognormal diffusion system, dt = h² (mass h³/dt per cell), from a smooth
+    initial field, each step a mixed solve to 1e-8 warm-started from the
+    last, on one handle."""
+    import numpy as np
+    import torch
+
+    import ldu_cases as lc
+
+    s = lc.config2(s=args.size, seed=0)
+    h = 1.0 / args.size
+    mass = np.full(s.n, h ** 3 / (1.0 * h * h))
+    A = pkg.ldu_create(s.n, *(torch.as_tensor(a, device=dev) for a in
+                              (s.owner, s.neighbour, s.diag + mass, s.upper, s.lower)),
+                       slice_rows=128)
+    m = torch.as_tensor(mass, device=dev)
+    # a smooth initial temperature, sin(pi x) sin(pi y) sin(pi z) at the cell centres
+    nx = args.size
+    c = np.asarray(s.cell_of)
+    ci, cj, ck = c % nx, (c // nx) % nx, c // (nx * nx)
+    T0 = torch.as_tensor(np.sin(np.pi * (ci + 0.5) / nx) * np.sin(np.pi * (cj + 0.5) / nx)
+                         * np.sin(np.pi * (ck + 0.5) / nx), device=dev)
+    T = T0.clone()
+    out = {}
+
+    def steps():
+        T.copy_(T0)
+        _, st, its, rr = pkg.ldu_heat_steps(A, m, T, 10, tol=TOL, precision="mixed")
+        out.update(status=st, iterations=its, relres_last=rr)
+
+    t = timed_fn(steps, 2, 1)
+    A.close()
+    return {"cells": s.n, "steps": 10, "dt_over_h2": 1.0, "s_per_step": statistics.median(t) / 10,
+            "iterations_per_step": out["iterations"] / 10, "relres_last": out["relres_last"],
+            "status": out["status"]}
 
 
 def run_autograd(args, dev, pkg, timed_fn):

@@ -210,6 +210,27 @@ int pipecg_solve(const ldu_matrix *A, const double *b, double *x, double tol, in
                  int precision, const pcg_opts *opts, int *iters, double *relres,
                  ldu_stream_t stream);
 
+/* nsteps backward-Euler steps of the heat equation (laplacianFoam's
+ * implicit step, Eq. 8): with the handle holding M + A (the diagonal mass
+ * term M = rho c V / dt added to the diffusion matrix, for instance through
+ * ldu_set_face_coeffs' diag_extra), each step solves
+ *     (M + A) T^(n+1) = M T^n
+ * starting from T^n, in place.  The handle and its repacked matrix are
+ * reused across steps; the right-hand side is formed by a kernel into a
+ * buffer of the handle (allocated on the first call).
+ *   mass        device double[n]: the diagonal M
+ *   T           device double[n]: T^0 in, T^nsteps out
+ *   precision   LDU_FP64 (Jacobi-PCG, as pcg_solve) or LDU_MIXED (as
+ *               pipecg_solve with LDU_MIXED and opts)
+ *   iters_total host, may be NULL: iterations summed over the steps
+ *   relres_last host, may be NULL: the last step's true relative residual
+ * Stops at the first step that does not return OK and returns its status.
+ * Single-system handles only (UNSUPPORTED on a batched handle).
+ * Synchronises stream after every step. */
+int ldu_heat_steps(ldu_matrix *A, const double *mass, double *T, int nsteps, double tol,
+                   int maxit, int precision, const pcg_opts *opts, int *iters_total,
+                   double *relres_last, ldu_stream_t stream);
+
 /* Gradient of a loss with respect to the face coefficients of
  * ldu_set_face_coeffs, given the adjoint solution lambda = A^-T dL/dx and
  * the forward solution x:  dcoef[f] = -(lambda[o] - lambda[n]) (x[o] - x[n])

@@ -7,6 +7,7 @@ and the autograd wrapper.  PyTorch supplies device memory and streams only.
 from .ldupcg import (LduError, LduMatrix, from_system, from_systems, ldu_batch_info,  # noqa: F401
                      ldu_batch_results, ldu_batch_schedule, ldu_create, ldu_create_batched,
                      ldu_destroy, ldu_diag_grad, ldu_harmonic_coeffs, ldu_harmonic_grad,
+                     ldu_heat_steps,
                      pcg_solve_batched, pcg_solve_batched_async,
                      ldu_face_grad, ldu_set_face_coeffs, ldu_spmv, ldu_update_values, lib,
                      library_path, pcg_solve, pcg_solve_ldu_noalloc, pipecg_solve,

@@ -120,6 +120,7 @@ struct ldu_matrix {
     ldu::SolveOut *out_dev;
     ldu::SolveOut *out_host;   // pinned host
     int *flags_dev;            // validation flags
+    double *rhs;               // right-hand side of ldu_heat_steps (allocated on first use)
     ldu_solve_stats last;
     struct ldu_batch *batch;   // systems of a batched handle (NULL otherwise)
 };

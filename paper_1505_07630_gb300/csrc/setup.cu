@@ -129,7 +129,7 @@ void free_handle(ldu_matrix *A) {
     ldu::free_batch(A);
     void *ptrs[] = {A->slice_ptr, A->slice_w, A->col, A->col16, A->fid, A->owner, A->neighbour,
                     A->val64, A->sd, A->isd, A->dg, A->val32, A->slots, A->bar_count,
-                    A->bar_err, A->out_dev, A->flags_dev, A->row_cell};
+                    A->bar_err, A->out_dev, A->flags_dev, A->row_cell, A->rhs};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);

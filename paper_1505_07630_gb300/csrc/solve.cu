@@ -39,6 +39,14 @@ using namespace ldu;
 
 namespace {
 
+// b = mass * T, the right-hand side of a backward-Euler step
+__global__ void k_mass_rhs(int64_t n, const double *__restrict__ mass,
+                           const double *__restrict__ T, double *__restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = mass[i] * T[i];
+}
+
 // ---------------------------------------------------------------------------
 // host side
 
@@ -254,6 +262,51 @@ extern "C" {
 int pcg_solve(const ldu_matrix *A, const double *b, double *x, double tol, int maxit, int *iters,
               double *relres, ldu_stream_t stream) {
     return run_solver(A, kPcg, b, x, tol, maxit, nullptr, iters, relres, (cudaStream_t)stream);
+}
+
+int ldu_heat_steps(ldu_matrix *A, const double *mass, double *T, int nsteps, double tol,
+                   int maxit, int precision, const pcg_opts *opts, int *iters_total,
+                   double *relres_last, ldu_stream_t stream) {
+    if (!A || nsteps < 0 || (A->n > 0 && (!mass || !T)) ||
+        (precision != LDU_FP64 && precision != LDU_MIXED))
+        return LDU_ERR_BAD_ARG;
+    if (A->row_cell)
+        return LDU_ERR_UNSUPPORTED;   // single-system handles only
+    cudaStream_t st = (cudaStream_t)stream;
+    if (iters_total)
+        *iters_total = 0;
+    if (relres_last)
+        *relres_last = 0.0;
+    if (A->n == 0 || nsteps == 0)
+        return LDU_OK;
+    if (!A->rhs) {
+        cudaError_t e = cudaMalloc((void **)&A->rhs, sizeof(double) * (size_t)A->n);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+        A->device_bytes += (int64_t)sizeof(double) * A->n;
+    }
+    int total = 0, rc = LDU_OK;
+    double rr = 0.0;
+    for (int step = 0; step < nsteps; ++step) {
+        // b = mass T^n; T^n is also the initial guess of T^(n+1)
+        k_mass_rhs<<<(int)std::min<int64_t>((A->n + 255) / 256, 1 << 20), 256, 0, st>>>(
+            A->n, mass, T, A->rhs);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return cuda_status(e);
+        int it = 0;
+        rc = precision == LDU_FP64
+                 ? run_solver(A, kPcg, A->rhs, T, tol, maxit, opts, &it, &rr, st)
+                 : run_solver(A, kMixed, A->rhs, T, tol, maxit, opts, &it, &rr, st);
+        total += it;
+        if (rc != LDU_OK)
+            break;
+    }
+    if (iters_total)
+        *iters_total = total;
+    if (relres_last)
+        *relres_last = rr;
+    return rc;
 }
 
 int pipecg_solve(const ldu_matrix *A, const double *b, double *x, double tol, int maxit,

@@ -92,6 +92,9 @@ def lib():
         L.ldu_face_grad.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.ldu_diag_grad.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.ldu_diag_grad.restype = i
+        L.ldu_heat_steps.argtypes = [_vp, _vp, _vp, i, d, i, i, ctypes.POINTER(PcgOpts), pi, pd,
+                                     _vp]
+        L.ldu_heat_steps.restype = i
         L.ldu_harmonic_coeffs.argtypes = [_vp] * 7
         L.ldu_harmonic_coeffs.restype = i
         L.ldu_harmonic_grad.argtypes = [_vp] * 8
@@ -302,6 +305,25 @@ def ldu_diag_grad(A, lam, x, out=None, stream=None):
                              _dev(out, torch.float64, A.n, "ddiag"), _stream(stream))
     _check(st, "ldu_diag_grad", allow_not_converged=False)
     return out
+
+
+def ldu_heat_steps(A, mass, T, nsteps, tol=1e-8, maxit=20000, precision="mixed", stream=None,
+                   check=True, **opts):
+    """nsteps backward-Euler heat steps (M + A) T^(n+1) = M T^n on a handle
+    that holds M + A, in place on T, each step warm-started from the last.
+    precision: 'fp64' (Jacobi-PCG) or 'mixed'.  Returns
+    (T, status, iterations over all steps, last true relative residual)."""
+    o = _pcg_opts(**opts)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    st = lib().ldu_heat_steps(A.handle, _dev(mass, torch.float64, A.n, "mass"),
+                              _dev(T, torch.float64, A.n, "T"), int(nsteps), float(tol),
+                              int(maxit), _PREC["fp64" if precision == "fp64" else "mixed"],
+                              ctypes.byref(o), ctypes.byref(it), ctypes.byref(rr),
+                              _stream(stream))
+    if check:
+        _check(st, "ldu_heat_steps")
+    return T, st, it.value, rr.value
 
 
 def ldu_harmonic_coeffs(A, k, g, bfac, coef=None, extra=None, stream=None):
