@@ -1,0 +1,110 @@
+"""Pins of the aggregation-AMG oracle (oracle/amg.py) against what the
+method and the mathematics fix: hand-worked aggregates, constant
+preservation of the prolongator, the Galerkin product, symmetry and
+definiteness of the V-cycle, agreement with a dense solve, and Table 2's
+magnitude (soft)."""
+import json
+import os
+from collections import deque
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import ldu_cases as lc
+from oracle import amg
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def test_chain_aggregates_by_hand():
+    """1 x 1 x 9 chain: roots 0, 3, 6 take their neighbours ({0,1}, {2,3,4},
+    {5,6,7}); row 8 has only the aggregated 7 and joins its aggregate."""
+    s = lc.poisson_box(9, 1, 1)
+    agg, na = amg.aggregate(amg.csr_of(s))
+    assert na == 3
+    assert agg.tolist() == [0, 0, 1, 1, 1, 2, 2, 2, 2]
+
+
+def test_isolated_rows_are_singletons():
+    A = sp.csr_matrix(np.diag([2.0, 3.0, 4.0]))
+    agg, na = amg.aggregate(A)
+    assert na == 3 and sorted(agg.tolist()) == [0, 1, 2]
+
+
+@pytest.mark.parametrize("make", [lambda: lc.poisson_box(9, 7, 5, diffusivity="lognormal", seed=2),
+                                  lambda: lc.config2(s=12), lambda: lc.config3(s=10)])
+def test_aggregates_partition_into_connected_sets(make):
+    s = make()
+    A = amg.csr_of(s)
+    agg, na = amg.aggregate(A)
+    assert agg.min() == 0 and agg.max() == na - 1
+    assert np.all(np.bincount(agg, minlength=na) > 0)
+    adj = [set(A.indices[A.indptr[i]:A.indptr[i + 1]]) - {i} for i in range(s.n)]
+    for a in range(na):
+        members = set(np.flatnonzero(agg == a).tolist())
+        start = next(iter(members))
+        seen, todo = {start}, deque([start])
+        while todo:
+            u = todo.popleft()
+            for v in adj[u] & members:
+                if v not in seen:
+                    seen.add(v)
+                    todo.append(v)
+        assert seen == members, a
+
+
+def test_prolongator_preserves_constants_on_neumann():
+    """A * 1 = 0 for the pure-Neumann Laplacian, so (I - w D^-1 A) P_t 1 = 1."""
+    s = lc.poisson_box(7, 6, 5, diffusivity="lognormal", seed=4, dirichlet=())
+    A = amg.csr_of(s)
+    assert np.max(np.abs(A @ np.ones(s.n))) <= 1e-12 * np.max(s.diag)
+    agg, na = amg.aggregate(A)
+    P = amg.prolongator(A, agg, na, amg.jacobi_weight(A))
+    assert np.allclose(P @ np.ones(na), 1.0, rtol=0, atol=1e-13)
+
+
+def test_jacobi_weight_is_four_thirds_over_the_gershgorin_bound():
+    """Interior rows of a unit-diffusivity Laplacian have sum |a_ij| / a_ii = 2."""
+    A = amg.csr_of(lc.poisson_box(6, 6, 6))
+    assert amg.jacobi_weight(A) == pytest.approx(2.0 / 3.0, rel=1e-14)
+
+
+def test_galerkin_coarse_matrix():
+    s = lc.poisson_box(6, 5, 4, diffusivity="lognormal", seed=5)
+    A = amg.csr_of(s)
+    levels, coarse = amg.hierarchy(A, max_coarse=10)
+    Ad = A.toarray()
+    for (Al, P, w), nxt in zip(levels, [lv[0] for lv in levels[1:]] + [sp.csr_matrix(coarse)]):
+        Pd = P.toarray()
+        ref = Pd.T @ Al.toarray() @ Pd
+        assert np.allclose(nxt.toarray(), ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
+    assert np.allclose(levels[0][0].toarray(), Ad)
+
+
+def test_vcycle_is_symmetric_positive_definite():
+    s = lc.config2(s=14)
+    levels, coarse = amg.hierarchy(amg.csr_of(s), max_coarse=40)
+    assert len(levels) >= 2
+    rng = np.random.default_rng(1)
+    for _ in range(3):
+        x, y = rng.standard_normal(s.n), rng.standard_normal(s.n)
+        vx, vy = amg.vcycle(levels, coarse, x), amg.vcycle(levels, coarse, y)
+        assert abs(vx @ y - x @ vy) <= 1e-12 * abs(vx @ y) + 1e-14
+        assert vx @ x > 0
+
+
+def test_amg_pcg_matches_dense_solve():
+    s = lc.poisson_box(10, 9, 8, diffusivity="lognormal", seed=6)
+    r = amg.amg_pcg(s, tol=1e-12, max_coarse=30)
+    assert r.levels >= 3 and r.relres <= 1e-12
+    xs = np.linalg.solve(amg.csr_of(s).toarray(), s.b)
+    assert np.linalg.norm(r.x - xs) <= 1e-9 * np.linalg.norm(xs)
+
+
+def test_table2_amg_magnitude():
+    """Soft: the paper's GPU AMG-CG takes 28 iterations at 64^3 (tol 1e-8)."""
+    ref = json.load(open(os.path.join(GOLDEN, "table2_iterations.json")))["GPU AMG-CG"]["64"]
+    r = amg.amg_pcg(lc.config1(s=64), tol=1e-8)
+    assert r.relres <= 1e-8
+    assert 0.5 * ref <= r.iters <= 2 * ref, r.iters
