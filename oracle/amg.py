@@ -12,8 +12,10 @@ around a distance-2 maximal independent set, with weighted Jacobi
              it and its neighbours form a new aggregate (the roots are a
              greedy distance-2 independent set);
     phase 2  every row still unaggregated joins the phase-1 aggregate of the
-             neighbour it is most strongly connected to (largest |a_ij|,
-             ties to the lower aggregate number);
+             neighbour it is most strongly connected to (largest |a_ij|;
+             values within a relative 1e-12 of the best count as ties,
+             which go to the lower aggregate number, so that rounding in
+             the coarse matrices cannot flip the choice);
     phase 3  rows with no aggregated neighbour (isolated rows) become
              aggregates of their own;
 * prolongator: the tentative P_t (P_t[i, agg(i)] = 1) smoothed by one
@@ -30,6 +32,9 @@ import numpy as np
 import scipy.sparse as sp
 
 
+TIE = 1e-12   # relative: connection strengths this close count as equal
+
+
 def csr_of(s, diag=None):
     """The system's matrix as a scipy CSR matrix (both triangles)."""
     n = s.n
@@ -41,8 +46,10 @@ def csr_of(s, diag=None):
 
 
 def aggregate(A):
-    """Aggregate number of every row (phases 1-3 above) and the count."""
-    A = sp.csr_matrix(A)
+    """Aggregate number of every row (phases 1-3 above) and the count.
+    Neighbours are visited in increasing column order."""
+    A = sp.csr_matrix(A, copy=True)
+    A.sort_indices()
     n = A.shape[0]
     indptr, indices, data = A.indptr, A.indices, A.data
     nbrs = [indices[indptr[i]:indptr[i + 1]] for i in range(n)]
@@ -66,8 +73,10 @@ def aggregate(A):
             if j == i or phase1[j] < 0:
                 continue
             a = abs(v)
-            if a > best_v or (a == best_v and phase1[j] < best):
+            if best < 0 or a > best_v * (1.0 + TIE):
                 best, best_v = phase1[j], a
+            elif a >= best_v * (1.0 - TIE) and phase1[j] < best:
+                best, best_v = phase1[j], max(a, best_v)
         agg[i] = best
     for i in range(n):                                   # phase 3
         if agg[i] < 0:
