@@ -423,8 +423,9 @@ def run_ours(args):
     batched = None
     if not args.skip_batched:
         batched = run_batched(args, dev, pkg, timed_fn=timed_generic)
-    pressure = autograd_case = heat = None
+    pressure = autograd_case = heat = amg_case = None
     if not args.skip_extra:
+        amg_case = run_amg(args, dev, pkg, s, timed_fn=timed_generic)
         pressure = run_pressure(args, dev, pkg, timed_fn=timed_generic)
         autograd_case = run_autograd(args, dev, pkg, timed_fn=timed_generic)
         heat = run_heat(args, dev, pkg, timed_fn=timed_generic)
@@ -471,6 +472,7 @@ def run_ours(args):
         "pressure256": pressure,
         "differentiable": autograd_case,
         "heat_steps": heat,
+        "amg_pcg": amg_case,
     }
     line.update(extra)
     emit(line, ranks)
@@ -530,6 +532,40 @@ def run_batched(args, dev, pkg, timed_fn):
             "grid_blocks": info["grid_blocks"], "teams_max": info["max_team"],
             "staged": staged_b,
             "ntasks": info["ntasks"]}
+
+
+def run_amg(args, dev, pkg, s, timed_fn):
+    """Aggregation-AMG preconditioned CG (Sec. 5, Table 2's AMG-CG) on the
+    headline system, FP64, to 1e-8: hierarchy setup (host, once per matrix),
+    one V-cycle, and the whole solve."""
+    import time
+
+    import torch
+
+    t0 = time.perf_counter()
+    M = pkg.amg_from_system(s, device=dev)
+    torch.cuda.synchronize(dev)
+    setup_s = time.perf_counter() - t0
+    b = torch.as_tensor(s.b, device=dev)
+    x = torch.zeros_like(b)
+    z = torch.empty_like(b)
+    res = {}
+
+    def solve():
+        res["out"] = pkg.amg_pcg_solve(M, b, x, tol=TOL, maxit=500)
+
+    def cycles():
+        for _ in range(10):
+            pkg.ldu_amg_vcycle(M, b, z)
+
+    t = timed_fn(solve, 2, 1, prep=x.zero_)
+    tv = timed_fn(cycles, 2, 1)
+    _, it, rr, st = res["out"]
+    out = {"s": statistics.median(t), "iters": it, "relres": rr, "status": st,
+           "setup_s": setup_s, "vcycle_ms": statistics.median(tv) * 100.0,
+           "levels": M.info()["rows"]}
+    M.close()
+    return out
 
 
 def run_pressure(args, dev, pkg, timed_fn):

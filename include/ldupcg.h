@@ -338,6 +338,72 @@ int pcg_solve_batched(const ldu_matrix *A, const double *b, double *x, double to
                       int precision, const pcg_opts *opts, int *iters, double *relres,
                       int *status, ldu_stream_t stream);
 
+/* ---- aggregation-AMG preconditioned CG (Sec. 5; Table 2's AMG-CG) ----
+ *
+ * The paper also preconditions CG with a V-cycle of an aggregation-based
+ * algebraic multigrid (aggregates grown around a distance-2 maximal
+ * independent set, weighted-Jacobi smoothing).  This library reads it as:
+ *   aggregation  rows in increasing order.  Phase 1: a row whose neighbours
+ *                (the off-diagonal non-zeros of its row) are all unaggregated
+ *                becomes a root and forms an aggregate with them.  Phase 2:
+ *                every other unaggregated row joins the phase-1 aggregate of
+ *                its strongest neighbour (largest |a_ij|; strengths within a
+ *                relative 1e-12 are ties, won by the lower aggregate number).
+ *                Phase 3: rows with no aggregated neighbour stand alone;
+ *   prolongator  P = (I - w D^-1 A) P_t with P_t the aggregates' indicator
+ *                and w = 4 / (3 rho), rho = max_i sum_j |a_ij| / a_ii;
+ *   hierarchy    A_c = P^T A P, repeated until a level has at most
+ *                max_coarse rows (or max_levels prolongators exist, or an
+ *                aggregation no longer shrinks the level); the coarsest level
+ *                is solved with its dense inverse;
+ *   cycle        V(1,1) from zero with the same weighted Jacobi;
+ *   outer        CG (Saad Alg. 9.1) with M^-1 r = V(r), stopping when the
+ *                recursive ||r||_2 <= tol ||b||_2 and the true residual
+ *                agrees (otherwise the search restarts from it).
+ * The hierarchy is built on the host once per matrix; the solve runs
+ * entirely in device kernels, the host reading two reductions per
+ * iteration to take the scalar decisions. */
+typedef struct ldu_amg ldu_amg;   /* opaque AMG hierarchy */
+
+typedef struct amg_opts {
+    int max_coarse;   /* coarsest-level rows at most this, 1..4096 (default 500) */
+    int max_levels;   /* prolongators at most this, 1..64 (default 12) */
+} amg_opts;
+
+/* Build the hierarchy of an LDU matrix.  Arguments as ldu_create (the fine
+ * level's handle is created with `opt`; coarse levels use 32-row slices).
+ * aopt: host, may be NULL.  Synchronises stream.  Errors as ldu_create;
+ * NOT_SPD if the coarsest matrix is singular; UNSUPPORTED if coarsening
+ * stops above 4096 rows. */
+int ldu_amg_create(int64_t n, int64_t nFaces, const int32_t *owner, const int32_t *neighbour,
+                   const double *diag, const double *upper, const double *lower,
+                   const ldu_opts *opt, const amg_opts *aopt, ldu_stream_t stream,
+                   ldu_amg **out);
+
+/* Free a hierarchy (waits for the device first); NULL is a no-op. */
+void ldu_amg_destroy(ldu_amg *M);
+
+/* Shape of a hierarchy: *levels = prolongators + 1; rows[l] and nnz[l]
+ * (host int64 arrays, each may be NULL) receive each level's rows and stored
+ * non-zeros (both triangles and the diagonal), for l < max_levels. */
+int ldu_amg_info(const ldu_amg *M, int *levels, int64_t *rows, int64_t *nnz, int max_levels);
+
+/* Aggregate number of every row of level `level` (host int32[rows of that
+ * level]); level must have a prolongator.  BAD_ARG otherwise. */
+int ldu_amg_aggregates(const ldu_amg *M, int level, int32_t *agg);
+
+/* x = V(b), one V(1,1) cycle from zero (b, x: device double[n], distinct).
+ * Queued on stream; allocates nothing. */
+int ldu_amg_vcycle(ldu_amg *M, const double *b, double *x, ldu_stream_t stream);
+
+/* AMG-preconditioned CG, FP64.  b: device double[n]; x: device double[n],
+ * initial guess in, solution out; iters, relres: host, may be NULL (relres
+ * is the true ||b - A x||_2 / ||b||_2 at exit).  NOT_SPD on a breakdown
+ * (p^T A p <= 0), NOT_CONVERGED when maxit is reached.  Synchronises
+ * stream (the host reads two reductions per iteration). */
+int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
+                  double *relres, ldu_stream_t stream);
+
 /* Jacobi-PCG on a small LDU system without any device allocation.  The paper
  * has no counterpart: this exists for callers that cannot call cudaMalloc
  * (their device memory is owned by another allocator, such as a framework's

@@ -4,7 +4,10 @@ The compute path is libldupcg (hand-written sm_103a CUDA behind a C ABI,
 include/ldupcg.h); this package holds its build script, the ctypes binding
 and the autograd wrapper.  PyTorch supplies device memory and streams only.
 """
-from .ldupcg import (LduError, LduMatrix, from_system, from_systems, ldu_batch_info,  # noqa: F401
+from .ldupcg import (LduAmg, LduError, LduMatrix, amg_from_system, amg_pcg_solve,  # noqa: F401
+                     ldu_amg_aggregates, ldu_amg_create, ldu_amg_destroy, ldu_amg_info,
+                     ldu_amg_vcycle)
+from .ldupcg import (from_system, from_systems, ldu_batch_info,  # noqa: F401
                      ldu_batch_results, ldu_batch_schedule, ldu_create, ldu_create_batched,
                      ldu_destroy, ldu_diag_grad, ldu_harmonic_coeffs, ldu_harmonic_grad,
                      ldu_heat_steps,

@@ -43,6 +43,10 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("max_team", ctypes.c_int), ("team_work_scale", ctypes.c_double)]
 
 
+class AmgOpts(ctypes.Structure):
+    _fields_ = [("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int)]
+
+
 class LduSolveStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
                 ("replacements", ctypes.c_int), ("relres", ctypes.c_double),
@@ -120,6 +124,19 @@ def lib():
         L.pcg_solve_batched.argtypes = [_vp, _vp, _vp, d, i, i, ctypes.POINTER(PcgOpts), _vp, _vp,
                                         _vp, _vp]
         L.pcg_solve_batched.restype = i
+        L.ldu_amg_create.argtypes = [i64, i64, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(LduOpts),
+                                     ctypes.POINTER(AmgOpts), _vp, ctypes.POINTER(_vp)]
+        L.ldu_amg_create.restype = i
+        L.ldu_amg_destroy.argtypes = [_vp]
+        L.ldu_amg_destroy.restype = None
+        L.ldu_amg_info.argtypes = [_vp, pi, _vp, _vp, i]
+        L.ldu_amg_info.restype = i
+        L.ldu_amg_aggregates.argtypes = [_vp, i, _vp]
+        L.ldu_amg_aggregates.restype = i
+        L.ldu_amg_vcycle.argtypes = [_vp, _vp, _vp, _vp]
+        L.ldu_amg_vcycle.restype = i
+        L.amg_pcg_solve.argtypes = [_vp, _vp, _vp, d, i, pi, pd, _vp]
+        L.amg_pcg_solve.restype = i
         L.ldu_status_string.argtypes = [i]
         L.ldu_status_string.restype = ctypes.c_char_p
         for name in ("ldu_create", "ldu_update_values", "ldu_set_face_coeffs", "ldu_spmv",
@@ -368,6 +385,116 @@ def from_system(sys_, device="cuda", **opts):
                    t(sys_.diag, torch.float64), t(sys_.upper, torch.float64),
                    t(sys_.lower, torch.float64), **opts)
     return A
+
+
+# ---- aggregation-AMG preconditioned CG ---------------------------------------
+
+class LduAmg:
+    """A device-resident AMG hierarchy (owner of its allocations)."""
+
+    def __init__(self, handle, n, device):
+        self._h = handle
+        self.n = n
+        self.device = device
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("LduAmg was destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ldu_amg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        """{'levels': L, 'rows': [...], 'nnz': [...]} of every level."""
+        import numpy as np
+        cap = 80
+        rows = np.zeros(cap, dtype=np.int64)
+        nnz = np.zeros(cap, dtype=np.int64)
+        lv = ctypes.c_int()
+        _check(lib().ldu_amg_info(self.handle, ctypes.byref(lv), _vp(rows.ctypes.data),
+                                  _vp(nnz.ctypes.data), cap), "ldu_amg_info")
+        L = lv.value
+        return {"levels": L, "rows": rows[:L].tolist(), "nnz": nnz[:L].tolist()}
+
+
+def ldu_amg_create(n, owner, neighbour, diag, upper, lower, max_coarse=0, max_levels=0,
+                   slice_rows=0, block_threads=0, blocks_per_sm=0, staging=0, min_slices=0,
+                   stream=None):
+    """Build the AMG hierarchy of an LDU matrix given as device tensors."""
+    nf = owner.numel()
+    args = [ctypes.c_int64(n), ctypes.c_int64(nf),
+            _dev(owner, torch.int32, nf, "owner"), _dev(neighbour, torch.int32, nf, "neighbour"),
+            _dev(diag, torch.float64, n, "diag"), _dev(upper, torch.float64, nf, "upper"),
+            _dev(lower, torch.float64, nf, "lower")]
+    opts = LduOpts(slice_rows, block_threads, blocks_per_sm, staging, min_slices)
+    aopts = AmgOpts(max_coarse, max_levels)
+    h = _vp()
+    st = lib().ldu_amg_create(*args, ctypes.byref(opts), ctypes.byref(aopts), _stream(stream),
+                              ctypes.byref(h))
+    _check(st, "ldu_amg_create", allow_not_converged=False)
+    return LduAmg(h, n, diag.device)
+
+
+def ldu_amg_destroy(M):
+    M.close()
+
+
+def ldu_amg_info(M):
+    return M.info()
+
+
+def ldu_amg_aggregates(M, level=0):
+    """Aggregate number of every row of a level (host int32 numpy array)."""
+    import numpy as np
+    rows = M.info()["rows"]
+    if not 0 <= level < len(rows) - 1:
+        raise ValueError(f"level {level} has no prolongator")
+    out = np.zeros(rows[level], dtype=np.int32)
+    _check(lib().ldu_amg_aggregates(M.handle, int(level), _vp(out.ctypes.data)),
+           "ldu_amg_aggregates", allow_not_converged=False)
+    return out
+
+
+def ldu_amg_vcycle(M, b, x=None, stream=None):
+    """x = V(b), one V(1,1) cycle from zero."""
+    if x is None:
+        x = torch.empty_like(b)
+    st = lib().ldu_amg_vcycle(M.handle, _dev(b, torch.float64, M.n, "b"),
+                              _dev(x, torch.float64, M.n, "x"), _stream(stream))
+    _check(st, "ldu_amg_vcycle", allow_not_converged=False)
+    return x
+
+
+def amg_pcg_solve(M, b, x=None, tol=1e-8, maxit=500, stream=None, check=True):
+    """AMG-preconditioned CG; returns (x, iters, relres, status)."""
+    if x is None:
+        x = torch.zeros_like(b)
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().amg_pcg_solve(M.handle, _dev(b, torch.float64, M.n, "b"),
+                             _dev(x, torch.float64, M.n, "x"), float(tol), int(maxit),
+                             ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+    if check:
+        _check(st, "amg_pcg_solve")
+    return x, it.value, rr.value, st
+
+
+def amg_from_system(sys_, device="cuda", **opts):
+    """Upload an ldu_cases.LduSystem and build its AMG hierarchy."""
+    t = lambda a, dt: torch.as_tensor(a).to(device=device, dtype=dt).contiguous()  # noqa: E731
+    return ldu_amg_create(sys_.n, t(sys_.owner, torch.int32), t(sys_.neighbour, torch.int32),
+                          t(sys_.diag, torch.float64), t(sys_.upper, torch.float64),
+                          t(sys_.lower, torch.float64), **opts)
 
 
 # ---- batches ----------------------------------------------------------------

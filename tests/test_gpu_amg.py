@@ -1,0 +1,169 @@
+"""Aggregation-AMG preconditioned CG (Sec. 5, Table 2's AMG-CG) through the
+C ABI against oracle/amg.py.
+
+Bars: the aggregates of every level and every level's row count are
+bit-exact (integer work; strengths within a relative 1e-12 count as ties on
+both sides, so rounding in the coarse matrices cannot flip a choice); one
+V-cycle agrees with the oracle's within 1e-11 relative to max |x| (the
+library applies A through its symmetrically scaled copy, whose entries
+carry a few ulps, and the coarsest solve is a dense inverse instead of an
+LU solve: both differences are rounding, amplified by at most the coarse
+levels' condition numbers, a few hundred here); the PCG's iteration count
+is within one of the oracle's and both meet the tolerance on the true
+residual."""
+import numpy as np
+import pytest
+
+import ldu_cases as lc
+from ldu_cases import configs, reorder
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    import paper_1505_07630_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def amg():
+    from oracle import amg as m
+    return m
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def rcm(s):
+    return reorder.renumber(s, reorder.rcm_order(s))
+
+
+CASES = {
+    "unit24": lambda: lc.poisson_box(24),
+    "lognormal_20x17x13": lambda: lc.poisson_box(20, 17, 13, diffusivity="lognormal", seed=3),
+    "lognormal_rcm24": lambda: rcm(lc.poisson_box(24, diffusivity="lognormal", seed=1)),
+    "graded32": lambda: configs.config1(32),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_hierarchy_and_aggregates_match_oracle(pkg, amg, name):
+    s = CASES[name]()
+    M = pkg.amg_from_system(s)
+    levels, coarse = amg.hierarchy(amg.csr_of(s))
+    info = M.info()
+    assert info["levels"] == len(levels) + 1
+    assert info["rows"] == [L[0].shape[0] for L in levels] + [coarse.shape[0]]
+    for lev, (Al, _, _) in enumerate(levels):
+        agg_o, _ = amg.aggregate(Al)
+        assert np.array_equal(pkg.ldu_amg_aggregates(M, lev), agg_o), lev
+    M.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_vcycle_matches_oracle(pkg, amg, name):
+    s = CASES[name]()
+    M = pkg.amg_from_system(s)
+    levels, coarse = amg.hierarchy(amg.csr_of(s))
+    rng = np.random.default_rng(7)
+    for b in (np.asarray(s.b, dtype=np.float64), rng.uniform(-1, 1, s.n)):
+        x = pkg.ldu_amg_vcycle(M, dev(b)).cpu().numpy()
+        xo = amg.vcycle(levels, coarse, b)
+        assert np.max(np.abs(x - xo)) <= 1e-11 * np.max(np.abs(xo))
+    M.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_amg_pcg_matches_oracle(pkg, amg, name):
+    s = CASES[name]()
+    M = pkg.amg_from_system(s)
+    r = amg.amg_pcg(s, tol=1e-8, maxit=200)
+    x, it, relres, st = pkg.amg_pcg_solve(M, dev(s.b), tol=1e-8, maxit=200)
+    assert st == 0
+    assert abs(it - r.iters) <= 1, (it, r.iters)
+    assert relres <= 1e-8 and r.relres <= 1e-8
+    # the true residual, recomputed from the returned x
+    A = amg.csr_of(s)
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(s.b - A @ xs) <= 1.0001e-8 * np.linalg.norm(s.b)
+    assert abs(relres - np.linalg.norm(s.b - A @ xs) / np.linalg.norm(s.b)) <= 1e-3 * relres + 1e-15
+    M.close()
+
+
+def test_amg_pcg_nonzero_initial_guess(pkg, amg):
+    s = lc.poisson_box(16, 14, 12, diffusivity="lognormal", seed=9)
+    M = pkg.amg_from_system(s)
+    x0 = np.random.default_rng(3).uniform(-1, 1, s.n)
+    x, it, relres, st = pkg.amg_pcg_solve(M, dev(s.b), x=dev(x0), tol=1e-9, maxit=200)
+    assert st == 0 and relres <= 1e-9 and it > 0
+    A = amg.csr_of(s)
+    assert np.linalg.norm(s.b - A @ x.cpu().numpy()) <= 1.0001e-9 * np.linalg.norm(s.b)
+
+
+def test_small_system_is_the_coarsest_level(pkg, amg):
+    """n <= max_coarse: no prolongator, the V-cycle is the exact inverse and
+    PCG converges in one iteration."""
+    s = lc.poisson_box(7, 6, 5, diffusivity="lognormal", seed=2)
+    M = pkg.amg_from_system(s)
+    assert M.info() == {"levels": 1, "rows": [s.n], "nnz": [s.n + 2 * len(s.owner)]}
+    b = np.asarray(s.b, dtype=np.float64)
+    x = pkg.ldu_amg_vcycle(M, dev(b)).cpu().numpy()
+    xd = np.linalg.solve(amg.csr_of(s).toarray(), b)
+    assert np.max(np.abs(x - xd)) <= 1e-12 * np.max(np.abs(xd))
+    _, it, relres, st = pkg.amg_pcg_solve(M, dev(b), tol=1e-10)
+    assert st == 0 and it == 1 and relres <= 1e-10
+    with pytest.raises(ValueError):
+        pkg.ldu_amg_aggregates(M, 0)
+    M.close()
+
+
+def test_max_levels_and_max_coarse(pkg, amg):
+    s = lc.poisson_box(24)
+    A = amg.csr_of(s)
+    for ml, mc in ((1, 500), (12, 2000), (12, 60)):
+        M = pkg.amg_from_system(s, max_levels=ml, max_coarse=mc)
+        levels, coarse = amg.hierarchy(A, max_coarse=mc, max_levels=ml)
+        assert M.info()["rows"] == [L[0].shape[0] for L in levels] + [coarse.shape[0]]
+        b = np.asarray(s.b, dtype=np.float64)
+        x = pkg.ldu_amg_vcycle(M, dev(b)).cpu().numpy()
+        xo = amg.vcycle(levels, coarse, b)
+        assert np.max(np.abs(x - xo)) <= 1e-11 * np.max(np.abs(xo))
+        M.close()
+
+
+def test_zero_rhs_and_bad_arguments(pkg):
+    s = lc.poisson_box(12)
+    M = pkg.amg_from_system(s)
+    x0 = torch.ones(s.n, dtype=torch.float64, device="cuda")
+    x, it, relres, st = pkg.amg_pcg_solve(M, torch.zeros_like(x0), x=x0)
+    assert st == 0 and it == 0 and relres == 0.0 and float(x.abs().max()) == 0.0
+    M.close()
+    with pytest.raises(pkg.LduError):
+        pkg.amg_from_system(s, max_coarse=5000)
+    with pytest.raises(pkg.LduError):
+        pkg.amg_from_system(s, max_levels=-1)
+    # coarsening stopped above the dense-inverse limit
+    with pytest.raises(pkg.LduError) as e:
+        pkg.amg_from_system(lc.poisson_box(48), max_levels=1)
+    assert e.value.status == -7
+
+
+def test_full_size_128_converges(pkg):
+    """The 128^3 graded Dirichlet Poisson system (Table 2's largest cube):
+    properties that hold at any size, without the oracle."""
+    s = configs.config2(128)
+    M = pkg.amg_from_system(s)
+    info = M.info()
+    assert info["rows"][0] == s.n and info["rows"][-1] <= 500
+    assert all(a > b for a, b in zip(info["rows"], info["rows"][1:]))
+    x, it, relres, st = pkg.amg_pcg_solve(M, dev(s.b), tol=1e-8, maxit=200)
+    assert st == 0 and relres <= 1e-8
+    assert it <= 60   # Table 2 reports 32 for the paper's aggregation AMG at 128^3
+    M.close()
