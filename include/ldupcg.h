@@ -370,15 +370,16 @@ typedef struct amg_opts {
     int max_levels;   /* prolongators at most this, 1..64 (default 12) */
 } amg_opts;
 
-/* Build the hierarchy of an LDU matrix.  Arguments as ldu_create (the fine
- * level's handle is created with `opt`; coarse levels use 32-row slices).
- * aopt: host, may be NULL.  Synchronises stream.  Errors as ldu_create;
- * NOT_SPD if the coarsest matrix is singular; UNSUPPORTED if coarsening
- * stops above 4096 rows. */
+/* Build the hierarchy of an LDU matrix.  n, nFaces, owner, neighbour,
+ * diag, upper, lower: as ldu_create (device arrays, copied to the host and
+ * validated there).  aopt: host, may be NULL.  Every level stores A's
+ * off-diagonal part in sliced ELL with 32-row slices, its diagonal, P as CSR
+ * and R = P^T as CSR.  Synchronises stream.  Errors as ldu_create; NOT_SPD
+ * if the coarsest matrix is singular; UNSUPPORTED if coarsening stops above
+ * 4096 rows. */
 int ldu_amg_create(int64_t n, int64_t nFaces, const int32_t *owner, const int32_t *neighbour,
                    const double *diag, const double *upper, const double *lower,
-                   const ldu_opts *opt, const amg_opts *aopt, ldu_stream_t stream,
-                   ldu_amg **out);
+                   const amg_opts *aopt, ldu_stream_t stream, ldu_amg **out);
 
 /* Free a hierarchy (waits for the device first); NULL is a no-op. */
 void ldu_amg_destroy(ldu_amg *M);
@@ -392,7 +393,8 @@ int ldu_amg_info(const ldu_amg *M, int *levels, int64_t *rows, int64_t *nnz, int
  * level]); level must have a prolongator.  BAD_ARG otherwise. */
 int ldu_amg_aggregates(const ldu_amg *M, int level, int32_t *agg);
 
-/* x = V(b), one V(1,1) cycle from zero (b, x: device double[n], distinct).
+/* x = V(b), one V(1,1) cycle from zero (b, x: device double[n], distinct;
+ * BAD_ARG if they are the same pointer).
  * Queued on stream; allocates nothing. */
 int ldu_amg_vcycle(ldu_amg *M, const double *b, double *x, ldu_stream_t stream);
 

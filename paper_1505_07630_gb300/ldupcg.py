@@ -124,8 +124,8 @@ def lib():
         L.pcg_solve_batched.argtypes = [_vp, _vp, _vp, d, i, i, ctypes.POINTER(PcgOpts), _vp, _vp,
                                         _vp, _vp]
         L.pcg_solve_batched.restype = i
-        L.ldu_amg_create.argtypes = [i64, i64, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(LduOpts),
-                                     ctypes.POINTER(AmgOpts), _vp, ctypes.POINTER(_vp)]
+        L.ldu_amg_create.argtypes = [i64, i64, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(AmgOpts),
+                                     _vp, ctypes.POINTER(_vp)]
         L.ldu_amg_create.restype = i
         L.ldu_amg_destroy.argtypes = [_vp]
         L.ldu_amg_destroy.restype = None
@@ -428,7 +428,6 @@ class LduAmg:
 
 
 def ldu_amg_create(n, owner, neighbour, diag, upper, lower, max_coarse=0, max_levels=0,
-                   slice_rows=0, block_threads=0, blocks_per_sm=0, staging=0, min_slices=0,
                    stream=None):
     """Build the AMG hierarchy of an LDU matrix given as device tensors."""
     nf = owner.numel()
@@ -436,11 +435,9 @@ def ldu_amg_create(n, owner, neighbour, diag, upper, lower, max_coarse=0, max_le
             _dev(owner, torch.int32, nf, "owner"), _dev(neighbour, torch.int32, nf, "neighbour"),
             _dev(diag, torch.float64, n, "diag"), _dev(upper, torch.float64, nf, "upper"),
             _dev(lower, torch.float64, nf, "lower")]
-    opts = LduOpts(slice_rows, block_threads, blocks_per_sm, staging, min_slices)
     aopts = AmgOpts(max_coarse, max_levels)
     h = _vp()
-    st = lib().ldu_amg_create(*args, ctypes.byref(opts), ctypes.byref(aopts), _stream(stream),
-                              ctypes.byref(h))
+    st = lib().ldu_amg_create(*args, ctypes.byref(aopts), _stream(stream), ctypes.byref(h))
     _check(st, "ldu_amg_create", allow_not_converged=False)
     return LduAmg(h, n, diag.device)
 
