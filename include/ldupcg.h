@@ -361,8 +361,8 @@ int pcg_solve_batched(const ldu_matrix *A, const double *b, double *x, double to
  *                recursive ||r||_2 <= tol ||b||_2 and the true residual
  *                agrees (otherwise the search restarts from it).
  * The hierarchy is built on the host once per matrix; the solve runs
- * entirely in device kernels, the host reading two reductions per
- * iteration to take the scalar decisions. */
+ * entirely in device kernels, its scalars (alpha, beta, the residual norms,
+ * the stopping decision) computed and kept on the device. */
 typedef struct ldu_amg ldu_amg;   /* opaque AMG hierarchy */
 
 typedef struct amg_opts {
@@ -393,18 +393,27 @@ int ldu_amg_info(const ldu_amg *M, int *levels, int64_t *rows, int64_t *nnz, int
  * level]); level must have a prolongator.  BAD_ARG otherwise. */
 int ldu_amg_aggregates(const ldu_amg *M, int level, int32_t *agg);
 
-/* x = V(b), one V(1,1) cycle from zero (b, x: device double[n], distinct;
- * BAD_ARG if they are the same pointer).
- * Queued on stream; allocates nothing. */
-int ldu_amg_vcycle(ldu_amg *M, const double *b, double *x, ldu_stream_t stream);
+/* x = V(b), one V(1,1) cycle from zero.  precision LDU_FP64: b, x are device
+ * double[n] and the cycle runs in double; LDU_FP32: device float[n], the
+ * cycle runs on the float copies of the level matrices.  b and x must be
+ * distinct (BAD_ARG if they are the same pointer).  Queued on stream;
+ * allocates nothing. */
+int ldu_amg_vcycle(ldu_amg *M, int precision, const void *b, void *x, ldu_stream_t stream);
 
-/* AMG-preconditioned CG, FP64.  b: device double[n]; x: device double[n],
- * initial guess in, solution out; iters, relres: host, may be NULL (relres
- * is the true ||b - A x||_2 / ||b||_2 at exit).  NOT_SPD on a breakdown
- * (p^T A p <= 0), NOT_CONVERGED when maxit is reached.  Synchronises
- * stream (the host reads two reductions per iteration). */
-int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
-                  double *relres, ldu_stream_t stream);
+/* AMG-preconditioned CG.  b: device double[n]; x: device double[n], initial
+ * guess in, solution out; iters, relres: host, may be NULL (relres is the
+ * true ||b - A x||_2 / ||b||_2 at exit).
+ *   precision  LDU_FP64: the cycle in double, Saad Alg. 9.1's beta (the
+ *              method as stated); LDU_MIXED: the cycle in float on float
+ *              copies of the level matrices, outer CG in double with the
+ *              Polak-Ribiere beta (r_new, z_new - z_old) / (r_old, z_old),
+ *              which keeps CG convergent under the float cycle's rounding;
+ *              the stopping test is on the double residual either way.
+ * NOT_SPD on a breakdown (p^T A p <= 0), NOT_CONVERGED when maxit is
+ * reached.  Synchronises stream: the host reads the device-resident scalars
+ * between batches of iterations sized from the observed convergence rate. */
+int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int precision,
+                  int *iters, double *relres, ldu_stream_t stream);
 
 /* Jacobi-PCG on a small LDU system without any device allocation.  The paper
  * has no counterpart: this exists for callers that cannot call cudaMalloc

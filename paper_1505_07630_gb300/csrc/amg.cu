@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "ldupcg_impl.cuh"
@@ -299,22 +300,30 @@ bool dense_inverse(const HCsr &A, std::vector<double> &inv) {
 
 // ---- device layouts ----------------------------------------------------------
 //
-// Every level keeps A's off-diagonal part in sliced ELL with 32-row slices
-// (one warp per slice, one thread per row, slot k of row s*32+i at
-// sp[s] + 32k + i; padding slots hold column 0 and value 0), its diagonal d
-// and w/d; P as CSR read one thread per row (3-5 entries a row); R = P^T as
-// CSR read one warp per row (tens to hundreds of entries a row).
+// The fine level keeps A's off-diagonal part in sliced ELL with 32-row
+// slices (one warp per slice, one thread per row, slot k of row s*32+i at
+// sp[s] + 32k + i; padding slots hold column 0 and value 0): a mesh's rows
+// are short and even, so padding is near zero and every load coalesces.
+// Coarse levels (tens of entries a row, uneven), P and R = P^T are CSR read
+// by groups of LPR lanes per row, LPR a power of two sized from the mean row
+// length.  Every level also keeps its diagonal d and w/d.  Values exist in
+// double and in float over one shared index structure: the FP64 cycle
+// follows the method in double; the mixed solve applies the cycle in float
+// (this GPU's FP64 pipe, about 2 FMAs per SM and clock, would otherwise bound
+// the sparse products) inside the FP64 outer CG.
 
+template <typename T>
 struct DSell {
     int n;
     const int *sp, *sw, *col;
-    const double *val;
+    const T *val;
 };
 
+template <typename T>
 struct DCsr {
     int n;
     const int *ptr, *col;
-    const double *val;
+    const T *val;
 };
 
 // scalars of the outer PCG, resident on the device between kernels
@@ -332,6 +341,12 @@ constexpr int kThreads = kWarps * 32;
 constexpr int kMaxBlocks = 152 * 8;       // grid cap: 8 resident blocks on each of 152 SMs
 
 __device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_down_sync(kFullMask, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1)
         v += __shfl_down_sync(kFullMask, v, o);
     return v;
@@ -397,27 +412,29 @@ __device__ bool grid_sum_last(const double (&v)[NV], double *part, unsigned *cou
 }
 
 // (r, z) of a new preconditioned residual: beta of the next direction, or
-// only (r, z) when the search restarts
-__device__ __forceinline__ void set_rz(AmgScalars *S, double rz) {
+// only (r, z) when the search restarts.  rzo = (r_new, z_old) gives the
+// Polak-Ribiere beta of flexible CG (the float cycle), 0 the Fletcher-Reeves
+// beta of Saad Alg. 9.1 (the FP64 cycle).
+__device__ __forceinline__ void set_rz(AmgScalars *S, double rz, double rzo) {
     if (S->restart) {
         S->rz = rz;
     } else {
-        S->beta = rz / S->rz;
+        S->beta = (rz - rzo) / S->rz;
         S->rz = rz;
     }
 }
 
-// sum over the off-diagonal slots of row `row` (slice s, lane i) of a_ij f(j)
-template <typename F>
-__device__ __forceinline__ double sell_row(const DSell &A, int s, int i, F f) {
+// sum over the off-diagonal slots of row s*32+i of a_ij f(j), in slot order
+template <typename T, typename F>
+__device__ __forceinline__ T sell_row(const DSell<T> &A, int s, int i, F f) {
     const int w = A.sw[s];
     const int base = A.sp[s] + i;
-    double acc = 0.0;
+    T acc = T(0);
     int k = 0;
     for (; k + 2 <= w; k += 2) {
         const int c0 = __ldg(A.col + base + k * 32), c1 = __ldg(A.col + base + (k + 1) * 32);
-        const double v0 = __ldcs(A.val + base + k * 32), v1 = __ldcs(A.val + base + (k + 1) * 32);
-        const double f0 = f(c0), f1 = f(c1);
+        const T v0 = __ldcs(A.val + base + k * 32), v1 = __ldcs(A.val + base + (k + 1) * 32);
+        const T f0 = f(c0), f1 = f(c1);
         acc = fma(v0, f0, acc);
         acc = fma(v1, f1, acc);
     }
@@ -430,130 +447,218 @@ __device__ __forceinline__ double sell_row(const DSell &A, int s, int i, F f) {
     for (int s = blockIdx.x * kWarps + (threadIdx.x >> 5), nsl = ((A).n + 31) >> 5; s < nsl; \
          s += gridDim.x * kWarps)
 
-// pre-smoothing from zero and the residual, in one pass:
-//   t = (w/d) b;  r = b - A t, with t_j formed from b_j on the fly
-__global__ void __launch_bounds__(kThreads) k_amg_pre(DSell A, const double *__restrict__ d,
-                                                      const double *__restrict__ wd,
-                                                      const double *__restrict__ b,
-                                                      double *__restrict__ t,
-                                                      double *__restrict__ r, const int *skip) {
+// rows of a CSR matrix by groups of LPR lanes: epi(row, sum_k val_k g(col_k),
+// pre(row)) in the group's first lane, pre(row) being loaded before the sum.
+// Rows are taken 32/LPR at a time per warp, so every lane of a warp reaches
+// each shuffle; each lane adds its entries (every LPR-th) in order.
+template <int LPR, typename T, typename Pre, typename G, typename E>
+__device__ __forceinline__ void csr_rows(const DCsr<T> &M, Pre pre, G g, E epi) {
+    constexpr int GPW = 32 / LPR;
+    const int lane = threadIdx.x & 31, grp = lane / LPR, gl = lane % LPR;
+    const int warp = (int)((blockIdx.x * kThreads + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * kThreads) >> 5);
+    for (int base = warp * GPW; base < M.n; base += nwarps * GPW) {
+        const int row = base + grp;
+        const bool lead = gl == 0 && row < M.n;
+        decltype(pre(0)) pv{};
+        if (lead)
+            pv = pre(row);
+        T acc = T(0);
+        if (row < M.n) {
+            const int e = M.ptr[row + 1];
+            for (int k = M.ptr[row] + gl; k < e; k += LPR)
+                acc = fma(__ldcs(M.val + k), g(__ldcs(M.col + k)), acc);
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1)
+            acc += __shfl_down_sync(kFullMask, acc, o, LPR);
+        if (lead)
+            epi(row, acc, pv);
+    }
+}
+
+template <typename T>
+struct Row3 {
+    T a, b, c;
+};
+
+// the residual after pre-smoothing from zero, t = (w/d) b having been
+// written by the producer of b:  r = b - A t
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_amg_pre(DSell<T> A, const T *__restrict__ d,
+                                                      const T *__restrict__ b,
+                                                      const T *__restrict__ t,
+                                                      T *__restrict__ r, const int *skip) {
     if (skip && *skip)
         return;
     const int lane = threadIdx.x & 31;
     FOR_SLICES(A) {
         const int row = s * 32 + lane;
-        const bool in = row < A.n;
-        const double off = sell_row(A, s, lane, [&](int c) { return wd[c] * b[c]; });
-        if (in) {
-            const double bi = b[row], ti = wd[row] * bi;
-            t[row] = ti;
-            r[row] = bi - fma(d[row], ti, off);
-        }
+        const T off = sell_row(A, s, lane, [&](int c) { return t[c]; });
+        if (row < A.n)
+            r[row] = b[row] - fma(d[row], t[row], off);
     }
 }
 
-// post-smoothing: x = t + (w/d) (b - A t); with DOT, also (b, x) reduced
-// into the outer PCG's scalars (b = r and x = z of the outer iteration)
-template <bool DOT>
-__global__ void __launch_bounds__(kThreads) k_amg_post(DSell A, const double *__restrict__ d,
-                                                       const double *__restrict__ wd,
-                                                       const double *__restrict__ b,
-                                                       const double *__restrict__ t,
-                                                       double *__restrict__ x, const int *skip,
+template <int LPR, typename T>
+__global__ void __launch_bounds__(kThreads) k_amg_pre_csr(DCsr<T> A, const T *__restrict__ d,
+                                                          const T *__restrict__ b,
+                                                          const T *__restrict__ t,
+                                                          T *__restrict__ r, const int *skip) {
+    if (skip && *skip)
+        return;
+    csr_rows<LPR>(
+        A, [&](int row) { return Row3<T>{b[row], d[row], t[row]}; }, [&](int c) { return t[c]; },
+        [&](int row, T off, Row3<T> v) { r[row] = v.a - fma(v.b, v.c, off); });
+}
+
+// post-smoothing: x = t + (w/d) (b - A t).  With DOT (level 0 inside the
+// outer PCG: b is the outer residual, x its preconditioned z) also
+// (r, z_new) and, with PR, (r, z_old) in FP64 from the double residual r64,
+// into the outer scalars
+template <typename T, bool DOT, bool PR>
+__global__ void __launch_bounds__(kThreads) k_amg_post(DSell<T> A, const T *__restrict__ d,
+                                                       const T *__restrict__ wd,
+                                                       const T *__restrict__ b,
+                                                       const T *__restrict__ t,
+                                                       T *__restrict__ x, const int *skip,
+                                                       const double *__restrict__ r64,
                                                        AmgScalars *S, double *part,
                                                        unsigned *count) {
     if (skip && *skip)
         return;
     const int lane = threadIdx.x & 31;
-    double dot = 0.0;
+    double dot = 0.0, doto = 0.0;
     FOR_SLICES(A) {
         const int row = s * 32 + lane;
-        const double off = sell_row(A, s, lane, [&](int c) { return t[c]; });
+        const T off = sell_row(A, s, lane, [&](int c) { return t[c]; });
         if (row < A.n) {
-            const double bi = b[row], ti = t[row];
-            const double xi = fma(wd[row], bi - fma(d[row], ti, off), ti);
+            const T bi = b[row], ti = t[row];
+            const T xi = fma(wd[row], bi - fma(d[row], ti, off), ti);
+            if (DOT) {
+                const double ri = r64[row];
+                if (PR)
+                    doto = fma(ri, (double)x[row], doto);
+                dot = fma(ri, (double)xi, dot);
+            }
             x[row] = xi;
-            if (DOT)
-                dot = fma(bi, xi, dot);
         }
     }
     if (DOT) {
-        double v[1] = {dot}, tot[1];
-        if (grid_sum_last<1>(v, part, count, tot) && threadIdx.x == 0)
-            set_rz(S, tot[0]);
+        double v[2] = {dot, doto}, tot[2];
+        if (grid_sum_last<2>(v, part, count, tot) && threadIdx.x == 0)
+            set_rz(S, tot[0], tot[1]);
     }
 }
 
-// b_c = R r, one warp per coarse row (fixed lane split and shuffle tree)
-__global__ void __launch_bounds__(kThreads) k_amg_restrict(DCsr R, const double *__restrict__ r,
-                                                           double *__restrict__ bc,
+template <int LPR, typename T>
+__global__ void __launch_bounds__(kThreads) k_amg_post_csr(DCsr<T> A, const T *__restrict__ d,
+                                                           const T *__restrict__ wd,
+                                                           const T *__restrict__ b,
+                                                           const T *__restrict__ t,
+                                                           T *__restrict__ x, const int *skip) {
+    if (skip && *skip)
+        return;
+    csr_rows<LPR>(
+        A, [&](int row) { return Row3<T>{b[row], d[row], t[row]}; }, [&](int c) { return t[c]; },
+        [&](int row, T off, Row3<T> v) { x[row] = fma(wd[row], v.a - fma(v.b, v.c, off), v.c); });
+}
+
+// b_c = R r, and t_c = (w/d)_c b_c for the coarse level's pre-smoothing
+// (wdc null when the coarse level is the coarsest)
+template <int LPR, typename T>
+__global__ void __launch_bounds__(kThreads) k_amg_restrict(DCsr<T> R, const T *__restrict__ r,
+                                                           const T *__restrict__ wdc,
+                                                           T *__restrict__ bc, T *__restrict__ tc,
                                                            const int *skip) {
     if (skip && *skip)
         return;
-    const int lane = threadIdx.x & 31;
-    for (int row = blockIdx.x * kWarps + (threadIdx.x >> 5); row < R.n;
-         row += gridDim.x * kWarps) {
-        double acc = 0.0;
-        for (int k = R.ptr[row] + lane; k < R.ptr[row + 1]; k += 32)
-            acc = fma(__ldcs(R.val + k), r[__ldcs(R.col + k)], acc);
-        acc = warp_sum(acc);
-        if (lane == 0)
-            bc[row] = acc;
-    }
+    csr_rows<LPR>(
+        R, [&](int row) { return wdc ? wdc[row] : T(0); }, [&](int c) { return r[c]; },
+        [&](int row, T v, T w) {
+            bc[row] = v;
+            if (wdc)
+                tc[row] = w * v;
+        });
 }
 
-// t += P x_c, one thread per fine row
-__global__ void __launch_bounds__(kThreads) k_amg_prolong(DCsr P, const double *__restrict__ xc,
-                                                          double *__restrict__ t,
-                                                          const int *skip) {
+// t += P x_c
+template <int LPR, typename T>
+__global__ void __launch_bounds__(kThreads) k_amg_prolong(DCsr<T> P, const T *__restrict__ xc,
+                                                          T *__restrict__ t, const int *skip) {
     if (skip && *skip)
         return;
-    for (int row = blockIdx.x * kThreads + threadIdx.x; row < P.n; row += gridDim.x * kThreads) {
-        double acc = t[row];
-        for (int k = P.ptr[row]; k < P.ptr[row + 1]; ++k)
-            acc = fma(__ldcs(P.val + k), xc[__ldcs(P.col + k)], acc);
-        t[row] = acc;
-    }
+    csr_rows<LPR>(
+        P, [&](int row) { return t[row]; }, [&](int c) { return xc[c]; },
+        [&](int row, T v, T t0) { t[row] = t0 + v; });
 }
 
 // x = Minv b on the coarsest level, one warp per row; with DOT (a system
-// that is its own coarsest level) also (b, x) into the outer scalars
-template <bool DOT>
-__global__ void __launch_bounds__(kThreads) k_amg_dense(int n, const double *__restrict__ Minv,
-                                                        const double *__restrict__ b,
-                                                        double *__restrict__ x, const int *skip,
+// that is its own coarsest level) also the outer PCG's dot products
+template <typename T, bool DOT, bool PR>
+__global__ void __launch_bounds__(kThreads) k_amg_dense(int n, const T *__restrict__ Minv,
+                                                        const T *__restrict__ b,
+                                                        T *__restrict__ x, const int *skip,
+                                                        const double *__restrict__ r64,
                                                         AmgScalars *S, double *part,
                                                         unsigned *count) {
     if (skip && *skip)
         return;
     const int lane = threadIdx.x & 31;
-    double dot = 0.0;
+    double dot = 0.0, doto = 0.0;
     for (int row = blockIdx.x * kWarps + (threadIdx.x >> 5); row < n; row += gridDim.x * kWarps) {
-        double s = 0.0;
+        T s = T(0);
         for (int k = lane; k < n; k += 32)
             s = fma(Minv[(size_t)row * n + k], b[k], s);
         s = warp_sum(s);
         if (lane == 0) {
+            if (DOT) {
+                const double ri = r64[row];
+                if (PR)
+                    doto = fma(ri, (double)x[row], doto);
+                dot = fma(ri, (double)s, dot);
+            }
             x[row] = s;
-            if (DOT)
-                dot = fma(b[row], s, dot);
         }
     }
     if (DOT) {
-        double v[1] = {dot}, tot[1];
-        if (grid_sum_last<1>(v, part, count, tot) && threadIdx.x == 0)
-            set_rz(S, tot[0]);
+        double v[2] = {dot, doto}, tot[2];
+        if (grid_sum_last<2>(v, part, count, tot) && threadIdx.x == 0)
+            set_rz(S, tot[0], tot[1]);
     }
 }
 
-// r = b - A x with (r, r) and (b, b) reduced: mode 0 starts a solve
-// (bn2, thr2, rr; the next direction restarts), mode 1 confirms a
-// converged recursive residual (rr only)
-__global__ void __launch_bounds__(kThreads) k_amg_residual(DSell A, const double *__restrict__ d,
+// the cycle's input from a double vector: t = (w/d) b (wd null: none) and,
+// for a float cycle, bv = b rounded (bv null: the cycle reads b itself)
+template <typename T>
+__device__ __forceinline__ void cycle_input(int i, double bi, const T *wd, T *t, T *bv) {
+    if (bv)
+        bv[i] = (T)bi;
+    if (wd)
+        t[i] = wd[i] * (T)bi;
+}
+
+// stand-alone cycle input
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_amg_scale(int n, const T *__restrict__ wd,
+                                                        const T *__restrict__ b,
+                                                        T *__restrict__ t) {
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads)
+        t[i] = wd[i] * b[i];
+}
+
+// r = b - A x (FP64) with (r, r) and (b, b) reduced, and the cycle's input
+// from r; mode 0 starts a solve (bn2, thr2, rr), mode 1 measures the true
+// residual (rr only); both make the next direction restart
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_amg_residual(DSell<double> A,
+                                                           const double *__restrict__ d,
                                                            const double *__restrict__ b,
                                                            const double *__restrict__ x,
-                                                           double *__restrict__ r, int mode,
-                                                           AmgScalars *S, double *part,
+                                                           double *__restrict__ r,
+                                                           const T *__restrict__ wd,
+                                                           T *__restrict__ t, T *__restrict__ bv,
+                                                           int mode, AmgScalars *S, double *part,
                                                            unsigned *count) {
     const int lane = threadIdx.x & 31;
     double rr = 0.0, bb = 0.0;
@@ -564,6 +669,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_residual(DSell A, const double
             const double bi = b[row];
             const double ri = bi - fma(d[row], x[row], off);
             r[row] = ri;
+            cycle_input(row, ri, wd, t, bv);
             rr = fma(ri, ri, rr);
             bb = fma(bi, bi, bb);
         }
@@ -581,14 +687,16 @@ __global__ void __launch_bounds__(kThreads) k_amg_residual(DSell A, const double
     }
 }
 
-__device__ __forceinline__ double next_p(double z, double beta, double p, int restart) {
-    return restart ? z : fma(beta, p, z);
+template <typename T>
+__device__ __forceinline__ double next_p(T z, double beta, double p, int restart) {
+    return restart ? (double)z : fma(beta, p, (double)z);
 }
 
 // p' = z + beta p (p' = z after a restart) and q = A p', p'_j formed on the
 // fly from z_j and p_j; (p', q) reduced into alpha
-__global__ void __launch_bounds__(kThreads) k_amg_q(DSell A, const double *__restrict__ d,
-                                                    const double *__restrict__ z,
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_amg_q(DSell<double> A, const double *__restrict__ d,
+                                                    const T *__restrict__ z,
                                                     const double *__restrict__ p,
                                                     double *__restrict__ pn,
                                                     double *__restrict__ q, AmgScalars *S,
@@ -624,13 +732,16 @@ __global__ void __launch_bounds__(kThreads) k_amg_q(DSell A, const double *__res
     }
 }
 
-// x += alpha p; r -= alpha q; (r, r) reduced; the iteration is counted and
-// the loop stops when the recursive residual meets the tolerance or maxit
-// iterations have run
+// x += alpha p; r -= alpha q and the cycle's input from r; (r, r) reduced;
+// the iteration is counted and the loop stops when the recursive residual
+// meets the tolerance or maxit iterations have run
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_amg_xr(int n, const double *__restrict__ p,
                                                      const double *__restrict__ q,
                                                      double *__restrict__ x,
-                                                     double *__restrict__ r, AmgScalars *S,
+                                                     double *__restrict__ r,
+                                                     const T *__restrict__ wd, T *__restrict__ t,
+                                                     T *__restrict__ bv, AmgScalars *S,
                                                      double *part, unsigned *count) {
     if (S->done)
         return;
@@ -640,6 +751,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_xr(int n, const double *__rest
         x[i] = fma(alpha, p[i], x[i]);
         const double ri = fma(-alpha, q[i], r[i]);
         r[i] = ri;
+        cycle_input(i, ri, wd, t, bv);
         rr = fma(ri, ri, rr);
     }
     double v[1] = {rr}, tot[1];
@@ -656,13 +768,46 @@ __global__ void __launch_bounds__(kThreads) k_amg_xr(int n, const double *__rest
     }
 }
 
-int grid_rows(int64_t n) {   // blocks for one warp per 32-row slice (or per row)
+int grid_rows(int64_t n) {   // blocks for one thread per row (one warp per 32-row slice)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, kMaxBlocks));
 }
 
 int grid_warps(int64_t n) {  // blocks for one warp per row
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kWarps - 1) / kWarps, kMaxBlocks));
 }
+
+int grid_lpr(int64_t n, int lpr) {   // blocks for lpr lanes per row
+    return (int)std::max<int64_t>(
+        1, std::min<int64_t>((n * lpr + kThreads - 1) / kThreads, kMaxBlocks));
+}
+
+// lanes per row: the power of two nearest a quarter of the mean row length, 1..32
+int lpr_for(int64_t rows, int64_t nnz) {
+    const double q = rows > 0 ? 0.25 * (double)nnz / (double)rows : 0.0;
+    int l = 1;
+    while (l < 32 && q >= l * 1.4142135623730951)
+        l *= 2;
+    return l;
+}
+
+// launchers of the CSR kernels at their lanes-per-row instance
+#define AMG_LPR_LAUNCHER(NAME, KERNEL)                                                    \
+    template <typename T, typename... Args>                                               \
+    void NAME(int lpr, int grid, cudaStream_t st, Args... args) {                         \
+        switch (lpr) {                                                                    \
+        case 1: KERNEL<1, T><<<grid, kThreads, 0, st>>>(args...); break;                  \
+        case 2: KERNEL<2, T><<<grid, kThreads, 0, st>>>(args...); break;                  \
+        case 4: KERNEL<4, T><<<grid, kThreads, 0, st>>>(args...); break;                  \
+        case 8: KERNEL<8, T><<<grid, kThreads, 0, st>>>(args...); break;                  \
+        case 16: KERNEL<16, T><<<grid, kThreads, 0, st>>>(args...); break;                \
+        default: KERNEL<32, T><<<grid, kThreads, 0, st>>>(args...); break;                \
+        }                                                                                 \
+    }
+AMG_LPR_LAUNCHER(launch_pre_csr, k_amg_pre_csr)
+AMG_LPR_LAUNCHER(launch_post_csr, k_amg_post_csr)
+AMG_LPR_LAUNCHER(launch_restrict, k_amg_restrict)
+AMG_LPR_LAUNCHER(launch_prolong, k_amg_prolong)
+#undef AMG_LPR_LAUNCHER
 
 template <typename T>
 cudaError_t upload(T **dst, const std::vector<T> &src, int64_t *bytes) {
@@ -675,6 +820,15 @@ cudaError_t upload(T **dst, const std::vector<T> &src, int64_t *bytes) {
     if (!src.empty())
         e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
     return e;
+}
+
+// a double array and its float rounding
+cudaError_t upload2(double **d64, float **d32, const std::vector<double> &src, int64_t *bytes) {
+    cudaError_t e = upload(d64, src, bytes);
+    if (e != cudaSuccess)
+        return e;
+    const std::vector<float> f(src.begin(), src.end());
+    return upload(d32, f, bytes);
 }
 
 template <typename T>
@@ -732,58 +886,102 @@ bool sell_of(const HCsr &A, HSell &S) {
 
 }  // namespace
 
+// the values and vectors of one level in one precision
+template <typename T>
+struct LevelVals {
+    T *a_val = nullptr, *d = nullptr, *wd = nullptr, *p_val = nullptr, *r_val = nullptr;
+    T *t = nullptr, *r = nullptr;   // smoothed iterate, residual
+    T *x = nullptr, *b = nullptr;   // level >= 1: cycle output and input
+};
+
 // one level above the coarsest
 struct amg_level {
     int64_t n = 0, nnz = 0;
     double w = 0.0;
-    int *a_sp = nullptr, *a_sw = nullptr, *a_col = nullptr;   // A off-diagonal, sliced ELL
-    double *a_val = nullptr, *d = nullptr, *wd = nullptr;      // values, diagonal, w / diagonal
-    int *p_ptr = nullptr, *p_col = nullptr;                    // P: n x n_next
-    double *p_val = nullptr;
-    int *r_ptr = nullptr, *r_col = nullptr;                    // R = P^T: n_next x n
-    double *r_val = nullptr;
-    double *t = nullptr, *r = nullptr;                         // smoothed iterate, residual
-    double *x = nullptr, *b = nullptr;                         // level >= 1: cycle output, input
-    std::vector<int32_t> agg;                                  // host copy, for inspection
-    DSell A() const { return DSell{(int)n, a_sp, a_sw, a_col, a_val}; }
+    // A's off-diagonal part: sliced ELL on level 0 (a_sp, a_sw), CSR on
+    // coarser levels (a_ptr)
+    int *a_sp = nullptr, *a_sw = nullptr, *a_ptr = nullptr, *a_col = nullptr;
+    int *p_ptr = nullptr, *p_col = nullptr;   // P: n x n_next
+    int *r_ptr = nullptr, *r_col = nullptr;   // R = P^T: n_next x n
+    int a_lpr = 1, p_lpr = 1, r_lpr = 1;      // lanes per row of the CSR reads
+    int64_t r_rows = 0;                       // rows of R (= next level's)
+    LevelVals<double> v64;
+    LevelVals<float> v32;
+    std::vector<int32_t> agg;                 // host copy, for inspection
+    template <typename T>
+    const LevelVals<T> &v() const;
+    template <typename T>
+    DSell<T> A() const { return DSell<T>{(int)n, a_sp, a_sw, a_col, v<T>().a_val}; }
+    template <typename T>
+    DCsr<T> Acsr() const { return DCsr<T>{(int)n, a_ptr, a_col, v<T>().a_val}; }
+    template <typename T>
+    DCsr<T> P() const { return DCsr<T>{(int)n, p_ptr, p_col, v<T>().p_val}; }
+    template <typename T>
+    DCsr<T> R() const { return DCsr<T>{(int)r_rows, r_ptr, r_col, v<T>().r_val}; }
+};
+template <>
+const LevelVals<double> &amg_level::v<double>() const { return v64; }
+template <>
+const LevelVals<float> &amg_level::v<float>() const { return v32; }
+
+template <typename T>
+struct CoarseVals {
+    T *inv = nullptr, *x = nullptr, *b = nullptr;
 };
 
 struct ldu_amg {
     int device = 0;
     int64_t n = 0;
     std::vector<amg_level> lev;     // every level that has a prolongator
-    // the fine matrix when it is itself the coarsest (no prolongator)
+    // the fine matrix in double for the outer CG (level 0's when it exists)
     int *f_sp = nullptr, *f_sw = nullptr, *f_col = nullptr;
     double *f_val = nullptr, *f_d = nullptr;
     int64_t nc = 0, c_nnz = 0;      // coarsest rows and non-zeros
-    double *cinv = nullptr;         // coarsest dense inverse (row-major)
-    double *cx = nullptr, *cb = nullptr;
+    CoarseVals<double> c64;         // coarsest dense inverse (row-major), vectors
+    CoarseVals<float> c32;
     double *r = nullptr, *z = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
+    float *r32 = nullptr, *z32 = nullptr;   // float cycle's input and output
     double *part = nullptr;
     unsigned *count = nullptr;
     AmgScalars *S = nullptr;        // device
     AmgScalars *S_host = nullptr;   // pinned
     int64_t device_bytes = 0;
-    DSell fine() const {
-        return lev.empty() ? DSell{(int)n, f_sp, f_sw, f_col, f_val} : lev[0].A();
+    template <typename T>
+    const CoarseVals<T> &c() const;
+    DSell<double> fine() const {
+        return lev.empty() ? DSell<double>{(int)n, f_sp, f_sw, f_col, f_val} : lev[0].A<double>();
     }
-    const double *fine_d() const { return lev.empty() ? f_d : lev[0].d; }
+    const double *fine_d() const { return lev.empty() ? f_d : lev[0].v64.d; }
 };
+template <>
+const CoarseVals<double> &ldu_amg::c<double>() const { return c64; }
+template <>
+const CoarseVals<float> &ldu_amg::c<float>() const { return c32; }
 
 namespace {
+
+template <typename T>
+void free_vals(LevelVals<T> &v) {
+    void *ptrs[] = {v.a_val, v.d, v.wd, v.p_val, v.r_val, v.t, v.r, v.x, v.b};
+    for (void *p : ptrs)
+        if (p)
+            cudaFree(p);
+}
 
 void free_amg(ldu_amg *M) {
     if (!M)
         return;
     for (auto &L : M->lev) {
-        void *ptrs[] = {L.a_sp, L.a_sw, L.a_col, L.a_val, L.d,     L.wd, L.p_ptr, L.p_col,
-                        L.p_val, L.r_ptr, L.r_col, L.r_val, L.t, L.r,  L.x,     L.b};
+        void *ptrs[] = {L.a_sp, L.a_sw, L.a_ptr, L.a_col, L.p_ptr, L.p_col, L.r_ptr, L.r_col};
         for (void *p : ptrs)
             if (p)
                 cudaFree(p);
+        free_vals(L.v64);
+        free_vals(L.v32);
     }
-    void *ptrs[] = {M->f_sp, M->f_sw, M->f_col, M->f_val, M->f_d, M->cinv, M->cx, M->cb,
-                    M->r,    M->z,    M->p[0],  M->p[1],  M->q,   M->part, M->count, M->S};
+    void *ptrs[] = {M->f_sp,   M->f_sw,   M->f_col,  M->f_val, M->f_d,    M->c64.inv, M->c64.x,
+                    M->c64.b,  M->c32.inv, M->c32.x, M->c32.b, M->r,      M->z,       M->p[0],
+                    M->p[1],   M->q,      M->r32,    M->z32,   M->part,   M->count,   M->S};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -792,41 +990,60 @@ void free_amg(ldu_amg *M) {
     delete M;
 }
 
-// x = V(b) from level l down (level 0: b and x are the caller's); with DOT the
-// last kernel also reduces (b, x) into the outer scalars
-int vcycle(ldu_amg *M, size_t l, const double *b, double *x, bool dot, const int *skip,
-           cudaStream_t st) {
+// x = V(b) from level l down, in precision T.  On entry the level's t holds
+// (w/d) b (the producer of b wrote it).  Level 0's b and x are the caller's;
+// with DOT the last kernel also reduces the outer PCG's dot products from
+// the double residual r64 (PR: the flexible-CG beta).
+template <typename T>
+int vcycle(ldu_amg *M, size_t l, const T *b, T *x, bool dot, const int *skip, cudaStream_t st) {
+    const bool pr = std::is_same<T, float>::value;
     if (l == M->lev.size()) {
-        if (dot)
-            k_amg_dense<true><<<grid_warps(M->nc), kThreads, 0, st>>>((int)M->nc, M->cinv, b, x,
-                                                                      skip, M->S, M->part,
-                                                                      M->count);
+        const CoarseVals<T> &C = M->c<T>();
+        const int g = grid_warps(M->nc);
+        if (!dot)
+            k_amg_dense<T, false, false><<<g, kThreads, 0, st>>>(
+                (int)M->nc, C.inv, b, x, skip, nullptr, nullptr, nullptr, nullptr);
+        else if (pr)
+            k_amg_dense<T, true, true><<<g, kThreads, 0, st>>>((int)M->nc, C.inv, b, x, skip, M->r,
+                                                               M->S, M->part, M->count);
         else
-            k_amg_dense<false><<<grid_warps(M->nc), kThreads, 0, st>>>(
-                (int)M->nc, M->cinv, b, x, skip, nullptr, nullptr, nullptr);
+            k_amg_dense<T, true, false><<<g, kThreads, 0, st>>>((int)M->nc, C.inv, b, x, skip,
+                                                                M->r, M->S, M->part, M->count);
         return cuda_status(cudaGetLastError());
     }
     const amg_level &L = M->lev[l];
-    const DSell A = L.A();
-    const int ga = grid_rows(L.n);
-    k_amg_pre<<<ga, kThreads, 0, st>>>(A, L.d, L.wd, b, L.t, L.r, skip);
+    const LevelVals<T> &V = L.v<T>();
+    if (l == 0)
+        k_amg_pre<T><<<grid_rows(L.n), kThreads, 0, st>>>(L.A<T>(), V.d, b, V.t, V.r, skip);
+    else
+        launch_pre_csr<T>(L.a_lpr, grid_lpr(L.n, L.a_lpr), st, L.Acsr<T>(), (const T *)V.d, b,
+                          (const T *)V.t, V.r, skip);
     const bool last = l + 1 == M->lev.size();
-    const int64_t nn = last ? M->nc : M->lev[l + 1].n;
-    double *bn = last ? M->cb : M->lev[l + 1].b;
-    double *xn = last ? M->cx : M->lev[l + 1].x;
-    k_amg_restrict<<<grid_warps(nn), kThreads, 0, st>>>(DCsr{(int)nn, L.r_ptr, L.r_col, L.r_val},
-                                                         L.r, bn, skip);
-    const int rc = vcycle(M, l + 1, bn, xn, false, skip, st);
+    T *bn = last ? M->c<T>().b : M->lev[l + 1].v<T>().b;
+    T *xn = last ? M->c<T>().x : M->lev[l + 1].v<T>().x;
+    const T *wdn = last ? nullptr : M->lev[l + 1].v<T>().wd;
+    T *tn = last ? nullptr : M->lev[l + 1].v<T>().t;
+    launch_restrict<T>(L.r_lpr, grid_lpr(L.r_rows, L.r_lpr), st, L.R<T>(), (const T *)V.r, wdn, bn,
+                       tn, skip);
+    const int rc = vcycle<T>(M, l + 1, bn, xn, false, skip, st);
     if (rc != LDU_OK)
         return rc;
-    k_amg_prolong<<<grid_rows(L.n), kThreads, 0, st>>>(DCsr{(int)L.n, L.p_ptr, L.p_col, L.p_val},
-                                                        xn, L.t, skip);
-    if (dot)
-        k_amg_post<true><<<ga, kThreads, 0, st>>>(A, L.d, L.wd, b, L.t, x, skip, M->S, M->part,
-                                                  M->count);
-    else
-        k_amg_post<false><<<ga, kThreads, 0, st>>>(A, L.d, L.wd, b, L.t, x, skip, nullptr,
-                                                   nullptr, nullptr);
+    launch_prolong<T>(L.p_lpr, grid_lpr(L.n, L.p_lpr), st, L.P<T>(), (const T *)xn, V.t, skip);
+    if (l == 0) {
+        const int g = grid_rows(L.n);
+        if (!dot)
+            k_amg_post<T, false, false><<<g, kThreads, 0, st>>>(
+                L.A<T>(), V.d, V.wd, b, V.t, x, skip, nullptr, nullptr, nullptr, nullptr);
+        else if (pr)
+            k_amg_post<T, true, true><<<g, kThreads, 0, st>>>(L.A<T>(), V.d, V.wd, b, V.t, x, skip,
+                                                              M->r, M->S, M->part, M->count);
+        else
+            k_amg_post<T, true, false><<<g, kThreads, 0, st>>>(
+                L.A<T>(), V.d, V.wd, b, V.t, x, skip, M->r, M->S, M->part, M->count);
+    } else {
+        launch_post_csr<T>(L.a_lpr, grid_lpr(L.n, L.a_lpr), st, L.Acsr<T>(), (const T *)V.d,
+                           (const T *)V.wd, b, (const T *)V.t, x, skip);
+    }
     return cuda_status(cudaGetLastError());
 }
 
@@ -836,6 +1053,115 @@ int read_scalars(ldu_amg *M, cudaStream_t st) {
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(st);
     return cuda_status(e);
+}
+
+// the outer PCG with the cycle in precision T (double: Saad Alg. 9.1 with
+// z = V(r); float: the same with the Polak-Ribiere beta)
+template <typename T>
+int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
+             double *relres, cudaStream_t st) {
+    const bool f32 = std::is_same<T, float>::value;
+    const DSell<double> A = M->fine();
+    const double *d = M->fine_d();
+    const int64_t n = M->n;
+    const int ga = grid_rows(n);
+    const T *wd0 = M->lev.empty() ? nullptr : M->lev[0].v<T>().wd;   // cycle input t0 = (w/d) r
+    T *t0 = M->lev.empty() ? nullptr : M->lev[0].v<T>().t;
+    T *bv = f32 ? (T *)M->r32 : nullptr;                  // float cycle: its own copy of r
+    const T *cyc_b = f32 ? (const T *)M->r32 : (const T *)M->r;
+    T *cyc_z = f32 ? (T *)M->z32 : (T *)M->z;
+    AmgScalars *S = M->S, *H = M->S_host;
+    std::memset(H, 0, sizeof(AmgScalars));
+    H->tol2 = tol * tol;
+    H->maxit = maxit;
+    H->status = LDU_OK;
+    cudaError_t e = cudaMemcpyAsync(S, H, sizeof(AmgScalars), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    int rc = LDU_OK;
+    // r = b - A x0, then z = V(r) and (r, z)
+    k_amg_residual<T><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, wd0, t0, bv, 0, S, M->part,
+                                               M->count);
+    if ((rc = vcycle<T>(M, 0, cyc_b, cyc_z, true, nullptr, st)) != LDU_OK)
+        return rc;
+    if ((rc = read_scalars(M, st)) != LDU_OK)
+        return rc;
+    int status = LDU_NOT_CONVERGED, it = 0, cur = 0;
+    bool confirmed = false;   // H->rr holds the true residual of the final x
+    const double bn2 = H->bn2, thr2 = H->thr2;
+    if (bn2 == 0.0) {
+        cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st);
+        status = LDU_OK;
+    } else if (H->rr <= thr2) {
+        status = LDU_OK;
+        confirmed = true;
+    } else if (maxit > 0) {
+        // iterations in batches between host reads, sized from the observed
+        // convergence rate so that few kernels run past the stopping point
+        double rr_prev = H->rr;
+        int it_prev = 0, batch = 4;
+        for (;;) {
+            for (int g = 0; g < batch; ++g) {
+                k_amg_q<T><<<ga, kThreads, 0, st>>>(A, d, (const T *)cyc_z, M->p[cur],
+                                                    M->p[cur ^ 1], M->q, S, M->part, M->count);
+                cur ^= 1;
+                k_amg_xr<T><<<ga, kThreads, 0, st>>>((int)n, M->p[cur], M->q, x, M->r, wd0, t0,
+                                                     bv, S, M->part, M->count);
+                if ((rc = vcycle<T>(M, 0, cyc_b, cyc_z, true, &S->done, st)) != LDU_OK)
+                    return rc;
+            }
+            if ((rc = read_scalars(M, st)) != LDU_OK)
+                return rc;
+            it = H->it;
+            if (H->status == LDU_ERR_NOT_SPD) {
+                status = LDU_ERR_NOT_SPD;
+                break;
+            }
+            if (H->conv) {
+                // confirm with the true residual; restart the search if it disagrees
+                k_amg_residual<T><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, wd0, t0, bv, 1, S,
+                                                           M->part, M->count);
+                if ((rc = read_scalars(M, st)) != LDU_OK)
+                    return rc;
+                if (H->rr <= thr2) {
+                    status = LDU_OK;
+                    confirmed = true;
+                    break;
+                }
+                if (it >= maxit)
+                    break;
+                if ((rc = vcycle<T>(M, 0, cyc_b, cyc_z, true, nullptr, st)) != LDU_OK)
+                    return rc;
+                continue;
+            }
+            if (H->status == LDU_NOT_CONVERGED)
+                break;
+            // remaining iterations from the mean contraction of ||r||^2
+            const double rho = std::pow(H->rr / rr_prev, 1.0 / std::max(1, it - it_prev));
+            double left = 8.0;
+            if (rho > 0.0 && rho < 1.0)
+                left = std::min(8.0, std::log(thr2 / H->rr) / std::log(rho));
+            batch = std::min(maxit - it, std::max(1, (int)std::lround(left)));
+            rr_prev = H->rr;
+            it_prev = it;
+        }
+    }
+    // the true residual at exit
+    double tr = 0.0;
+    if (bn2 > 0.0 && confirmed) {
+        tr = std::sqrt(H->rr / bn2);
+    } else if (bn2 > 0.0) {
+        k_amg_residual<T><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, nullptr, nullptr, nullptr, 1,
+                                                   S, M->part, M->count);
+        if ((rc = read_scalars(M, st)) != LDU_OK)
+            return rc;
+        tr = std::sqrt(H->rr / bn2);
+    }
+    if (iters)
+        *iters = it;
+    if (relres)
+        *relres = tr;
+    return status;
 }
 
 }  // namespace
@@ -904,7 +1230,7 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
             return cuda_status(e); \
         }                          \
     } while (0)
-    bool fine_uploaded = false;
+    int64_t *nb = &M->device_bytes;
     // coarsen while the level is above max_coarse rows and aggregation shrinks it
     while (A.n > max_coarse && (int)M->lev.size() < max_levels) {
         std::vector<int32_t> agg;
@@ -924,39 +1250,65 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
         }
         HCsr Ac = galerkin(A, P, R);
         L.agg = std::move(agg);
-        HSell S;
-        if (!sell_of(A, S)) {
-            free_amg(M);
-            return LDU_ERR_UNSUPPORTED;
-        }
         std::vector<double> d((size_t)A.n), wd((size_t)A.n);
         for (int64_t i = 0; i < A.n; ++i) {
             d[(size_t)i] = diag_of(A, i);
             wd[(size_t)i] = L.w / d[(size_t)i];
         }
-        std::vector<int> pp(P.ptr.begin(), P.ptr.end()), rp(R.ptr.begin(), R.ptr.end());
-        CKA(upload(&L.a_sp, S.sp, &M->device_bytes));
-        CKA(upload(&L.a_sw, S.sw, &M->device_bytes));
-        CKA(upload(&L.a_col, S.col, &M->device_bytes));
-        CKA(upload(&L.a_val, S.val, &M->device_bytes));
-        CKA(upload(&L.d, d, &M->device_bytes));
-        CKA(upload(&L.wd, wd, &M->device_bytes));
-        CKA(upload(&L.p_ptr, pp, &M->device_bytes));
-        CKA(upload(&L.p_col, P.col, &M->device_bytes));
-        CKA(upload(&L.p_val, P.val, &M->device_bytes));
-        CKA(upload(&L.r_ptr, rp, &M->device_bytes));
-        CKA(upload(&L.r_col, R.col, &M->device_bytes));
-        CKA(upload(&L.r_val, R.val, &M->device_bytes));
-        CKA(alloc(&L.t, L.n, &M->device_bytes));
-        CKA(alloc(&L.r, L.n, &M->device_bytes));
-        if (M->lev.size() > 1) {
-            CKA(alloc(&L.x, L.n, &M->device_bytes));
-            CKA(alloc(&L.b, L.n, &M->device_bytes));
+        if (M->lev.size() == 1) {
+            HSell S;
+            if (!sell_of(A, S)) {
+                free_amg(M);
+                return LDU_ERR_UNSUPPORTED;
+            }
+            CKA(upload(&L.a_sp, S.sp, nb));
+            CKA(upload(&L.a_sw, S.sw, nb));
+            CKA(upload(&L.a_col, S.col, nb));
+            CKA(upload2(&L.v64.a_val, &L.v32.a_val, S.val, nb));
+        } else {
+            // off-diagonal CSR of a coarse level
+            std::vector<int> ap((size_t)A.n + 1, 0), ac;
+            std::vector<double> av;
+            ac.reserve(A.col.size());
+            av.reserve(A.col.size());
+            for (int64_t i = 0; i < A.n; ++i) {
+                for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k)
+                    if (A.col[(size_t)k] != i) {
+                        ac.push_back(A.col[(size_t)k]);
+                        av.push_back(A.val[(size_t)k]);
+                    }
+                ap[(size_t)i + 1] = (int)ac.size();
+            }
+            L.a_lpr = lpr_for(A.n, (int64_t)ac.size());
+            CKA(upload(&L.a_ptr, ap, nb));
+            CKA(upload(&L.a_col, ac, nb));
+            CKA(upload2(&L.v64.a_val, &L.v32.a_val, av, nb));
         }
-        fine_uploaded = true;
+        L.p_lpr = lpr_for(P.n, (int64_t)P.col.size());
+        L.r_lpr = lpr_for(R.n, (int64_t)R.col.size());
+        L.r_rows = R.n;
+        std::vector<int> pp(P.ptr.begin(), P.ptr.end()), rp(R.ptr.begin(), R.ptr.end());
+        CKA(upload2(&L.v64.d, &L.v32.d, d, nb));
+        CKA(upload2(&L.v64.wd, &L.v32.wd, wd, nb));
+        CKA(upload(&L.p_ptr, pp, nb));
+        CKA(upload(&L.p_col, P.col, nb));
+        CKA(upload2(&L.v64.p_val, &L.v32.p_val, P.val, nb));
+        CKA(upload(&L.r_ptr, rp, nb));
+        CKA(upload(&L.r_col, R.col, nb));
+        CKA(upload2(&L.v64.r_val, &L.v32.r_val, R.val, nb));
+        CKA(alloc(&L.v64.t, L.n, nb));
+        CKA(alloc(&L.v64.r, L.n, nb));
+        CKA(alloc(&L.v32.t, L.n, nb));
+        CKA(alloc(&L.v32.r, L.n, nb));
+        if (M->lev.size() > 1) {
+            CKA(alloc(&L.v64.x, L.n, nb));
+            CKA(alloc(&L.v64.b, L.n, nb));
+            CKA(alloc(&L.v32.x, L.n, nb));
+            CKA(alloc(&L.v32.b, L.n, nb));
+        }
         A = std::move(Ac);
     }
-    if (!fine_uploaded) {
+    if (M->lev.empty()) {
         // the fine matrix is the coarsest: keep its SpMV form for the outer loop
         HSell S;
         if (!sell_of(A, S)) {
@@ -966,11 +1318,11 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
         std::vector<double> d((size_t)A.n);
         for (int64_t i = 0; i < A.n; ++i)
             d[(size_t)i] = diag_of(A, i);
-        CKA(upload(&M->f_sp, S.sp, &M->device_bytes));
-        CKA(upload(&M->f_sw, S.sw, &M->device_bytes));
-        CKA(upload(&M->f_col, S.col, &M->device_bytes));
-        CKA(upload(&M->f_val, S.val, &M->device_bytes));
-        CKA(upload(&M->f_d, d, &M->device_bytes));
+        CKA(upload(&M->f_sp, S.sp, nb));
+        CKA(upload(&M->f_sw, S.sw, nb));
+        CKA(upload(&M->f_col, S.col, nb));
+        CKA(upload(&M->f_val, S.val, nb));
+        CKA(upload(&M->f_d, d, nb));
     }
     // the coarsest level, applied through its dense inverse
     if (A.n > kMaxCoarse) {
@@ -984,18 +1336,22 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
         free_amg(M);
         return LDU_ERR_NOT_SPD;
     }
-    CKA(upload(&M->cinv, inv, &M->device_bytes));
-    CKA(alloc(&M->cx, A.n, &M->device_bytes));
-    CKA(alloc(&M->cb, A.n, &M->device_bytes));
-    CKA(alloc(&M->r, n, &M->device_bytes));
-    CKA(alloc(&M->z, n, &M->device_bytes));
-    CKA(alloc(&M->p[0], n, &M->device_bytes));
-    CKA(alloc(&M->p[1], n, &M->device_bytes));
-    CKA(alloc(&M->q, n, &M->device_bytes));
-    CKA(alloc(&M->part, 2 * kMaxBlocks, &M->device_bytes));
-    CKA(alloc(&M->count, 1, &M->device_bytes));
+    CKA(upload2(&M->c64.inv, &M->c32.inv, inv, nb));
+    CKA(alloc(&M->c64.x, A.n, nb));
+    CKA(alloc(&M->c64.b, A.n, nb));
+    CKA(alloc(&M->c32.x, A.n, nb));
+    CKA(alloc(&M->c32.b, A.n, nb));
+    CKA(alloc(&M->r, n, nb));
+    CKA(alloc(&M->z, n, nb));
+    CKA(alloc(&M->p[0], n, nb));
+    CKA(alloc(&M->p[1], n, nb));
+    CKA(alloc(&M->q, n, nb));
+    CKA(alloc(&M->r32, n, nb));
+    CKA(alloc(&M->z32, n, nb));
+    CKA(alloc(&M->part, 2 * kMaxBlocks, nb));
+    CKA(alloc(&M->count, 1, nb));
     CKA(cudaMemset(M->count, 0, sizeof(unsigned)));
-    CKA(alloc(&M->S, 1, &M->device_bytes));
+    CKA(alloc(&M->S, 1, nb));
     CKA(cudaMallocHost((void **)&M->S_host, sizeof(AmgScalars)));
 #undef CKA
     *out = M;
@@ -1031,111 +1387,31 @@ int ldu_amg_aggregates(const ldu_amg *M, int level, int32_t *agg) {
     return LDU_OK;
 }
 
-int ldu_amg_vcycle(ldu_amg *M, const double *b, double *x, ldu_stream_t stream) {
-    if (!M || !b || !x || b == x)
-        return LDU_ERR_BAD_ARG;
-    return vcycle(M, 0, b, x, false, nullptr, (cudaStream_t)stream);
-}
-
-int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
-                  double *relres, ldu_stream_t stream) {
-    if (!M || !b || !x || b == x || maxit < 0 || !(tol >= 0.0))
+int ldu_amg_vcycle(ldu_amg *M, int precision, const void *b, void *x, ldu_stream_t stream) {
+    if (!M || !b || !x || b == x || (precision != LDU_FP64 && precision != LDU_FP32))
         return LDU_ERR_BAD_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const DSell A = M->fine();
-    const double *d = M->fine_d();
-    const int64_t n = M->n;
-    const int ga = grid_rows(n);
-    AmgScalars *S = M->S, *H = M->S_host;
-    std::memset(H, 0, sizeof(AmgScalars));
-    H->tol2 = tol * tol;
-    H->maxit = maxit;
-    H->status = LDU_OK;
-    cudaError_t e = cudaMemcpyAsync(S, H, sizeof(AmgScalars), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess)
-        return cuda_status(e);
-    int rc = LDU_OK;
-    // r = b - A x0, then z = V(r) and (r, z)
-    k_amg_residual<<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, 0, S, M->part, M->count);
-    if ((rc = vcycle(M, 0, M->r, M->z, true, nullptr, st)) != LDU_OK)
-        return rc;
-    if ((rc = read_scalars(M, st)) != LDU_OK)
-        return rc;
-    int status = LDU_NOT_CONVERGED, it = 0, cur = 0;
-    bool confirmed = false;   // H->rr holds the true residual of the final x
-    const double bn2 = H->bn2, thr2 = H->thr2;
-    if (bn2 == 0.0) {
-        cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st);
-        status = LDU_OK;
-    } else if (H->rr <= thr2) {
-        status = LDU_OK;
-    } else if (maxit == 0) {
-        status = LDU_NOT_CONVERGED;
-    } else {
-        // iterations in batches between host reads, sized from the observed
-        // convergence rate so that few kernels run past the stopping point
-        double rr_prev = H->rr;
-        int it_prev = 0, batch = 4;
-        for (;;) {
-            for (int g = 0; g < batch; ++g) {
-                k_amg_q<<<ga, kThreads, 0, st>>>(A, d, M->z, M->p[cur], M->p[cur ^ 1], M->q, S,
-                                                 M->part, M->count);
-                cur ^= 1;
-                k_amg_xr<<<grid_rows(n), kThreads, 0, st>>>((int)n, M->p[cur], M->q, x, M->r, S,
-                                                            M->part, M->count);
-                if ((rc = vcycle(M, 0, M->r, M->z, true, &S->done, st)) != LDU_OK)
-                    return rc;
-            }
-            if ((rc = read_scalars(M, st)) != LDU_OK)
-                return rc;
-            it = H->it;
-            if (H->status == LDU_ERR_NOT_SPD) {
-                status = LDU_ERR_NOT_SPD;
-                break;
-            }
-            if (H->conv) {
-                // confirm with the true residual; restart the search if it disagrees
-                k_amg_residual<<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, 1, S, M->part, M->count);
-                if ((rc = read_scalars(M, st)) != LDU_OK)
-                    return rc;
-                if (H->rr <= thr2) {
-                    status = LDU_OK;
-                    confirmed = true;
-                    break;
-                }
-                if ((rc = vcycle(M, 0, M->r, M->z, true, nullptr, st)) != LDU_OK)
-                    return rc;
-                if (it >= maxit)
-                    break;
-                continue;
-            }
-            if (H->status == LDU_NOT_CONVERGED)
-                break;
-            // remaining iterations from the mean contraction of ||r||^2
-            const double rho = std::pow(H->rr / rr_prev, 1.0 / std::max(1, it - it_prev));
-            double left = 8.0;
-            if (rho > 0.0 && rho < 1.0)
-                left = std::min(8.0, std::log(thr2 / H->rr) / std::log(rho));
-            batch = std::min(maxit - it, std::max(1, (int)std::lround(left)));
-            rr_prev = H->rr;
-            it_prev = it;
-        }
+    const int g = grid_rows(M->n);
+    if (precision == LDU_FP64) {
+        if (!M->lev.empty())
+            k_amg_scale<double><<<g, kThreads, 0, st>>>((int)M->n, M->lev[0].v64.wd,
+                                                        (const double *)b, M->lev[0].v64.t);
+        return vcycle<double>(M, 0, (const double *)b, (double *)x, false, nullptr, st);
     }
-    // the true residual at exit
-    double tr = 0.0;
-    if (bn2 > 0.0 && (confirmed || (status == LDU_OK && it == 0))) {
-        tr = std::sqrt(H->rr / bn2);
-    } else if (bn2 > 0.0) {
-        k_amg_residual<<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, 1, S, M->part, M->count);
-        if ((rc = read_scalars(M, st)) != LDU_OK)
-            return rc;
-        tr = std::sqrt(H->rr / bn2);
-    }
-    if (iters)
-        *iters = it;
-    if (relres)
-        *relres = tr;
-    return status;
+    if (!M->lev.empty())
+        k_amg_scale<float><<<g, kThreads, 0, st>>>((int)M->n, M->lev[0].v32.wd, (const float *)b,
+                                                   M->lev[0].v32.t);
+    return vcycle<float>(M, 0, (const float *)b, (float *)x, false, nullptr, st);
+}
+
+int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int precision,
+                  int *iters, double *relres, ldu_stream_t stream) {
+    if (!M || !b || !x || b == x || maxit < 0 || !(tol >= 0.0) ||
+        (precision != LDU_FP64 && precision != LDU_MIXED))
+        return LDU_ERR_BAD_ARG;
+    if (precision == LDU_FP64)
+        return pcg_loop<double>(M, b, x, tol, maxit, iters, relres, (cudaStream_t)stream);
+    return pcg_loop<float>(M, b, x, tol, maxit, iters, relres, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -133,9 +133,9 @@ def lib():
         L.ldu_amg_info.restype = i
         L.ldu_amg_aggregates.argtypes = [_vp, i, _vp]
         L.ldu_amg_aggregates.restype = i
-        L.ldu_amg_vcycle.argtypes = [_vp, _vp, _vp, _vp]
+        L.ldu_amg_vcycle.argtypes = [_vp, i, _vp, _vp, _vp]
         L.ldu_amg_vcycle.restype = i
-        L.amg_pcg_solve.argtypes = [_vp, _vp, _vp, d, i, pi, pd, _vp]
+        L.amg_pcg_solve.argtypes = [_vp, _vp, _vp, d, i, i, pi, pd, _vp]
         L.amg_pcg_solve.restype = i
         L.ldu_status_string.argtypes = [i]
         L.ldu_status_string.restype = ctypes.c_char_p
@@ -463,23 +463,28 @@ def ldu_amg_aggregates(M, level=0):
 
 
 def ldu_amg_vcycle(M, b, x=None, stream=None):
-    """x = V(b), one V(1,1) cycle from zero."""
+    """x = V(b), one V(1,1) cycle from zero, in b's precision (float64 or float32)."""
+    if b.dtype not in (torch.float64, torch.float32):
+        raise ValueError("b must be float64 or float32")
     if x is None:
         x = torch.empty_like(b)
-    st = lib().ldu_amg_vcycle(M.handle, _dev(b, torch.float64, M.n, "b"),
-                              _dev(x, torch.float64, M.n, "x"), _stream(stream))
+    prec = FP64 if b.dtype == torch.float64 else FP32
+    st = lib().ldu_amg_vcycle(M.handle, prec, _dev(b, b.dtype, M.n, "b"),
+                              _dev(x, b.dtype, M.n, "x"), _stream(stream))
     _check(st, "ldu_amg_vcycle", allow_not_converged=False)
     return x
 
 
-def amg_pcg_solve(M, b, x=None, tol=1e-8, maxit=500, stream=None, check=True):
-    """AMG-preconditioned CG; returns (x, iters, relres, status)."""
+def amg_pcg_solve(M, b, x=None, tol=1e-8, maxit=500, precision="fp64", stream=None, check=True):
+    """AMG-preconditioned CG (precision "fp64" or "mixed"); returns
+    (x, iters, relres, status)."""
     if x is None:
         x = torch.zeros_like(b)
+    prec = {"fp64": FP64, "mixed": MIXED}[precision]
     it = ctypes.c_int()
     rr = ctypes.c_double()
     st = lib().amg_pcg_solve(M.handle, _dev(b, torch.float64, M.n, "b"),
-                             _dev(x, torch.float64, M.n, "x"), float(tol), int(maxit),
+                             _dev(x, torch.float64, M.n, "x"), float(tol), int(maxit), prec,
                              ctypes.byref(it), ctypes.byref(rr), _stream(stream))
     if check:
         _check(st, "amg_pcg_solve")

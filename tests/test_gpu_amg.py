@@ -10,7 +10,15 @@ carry a few ulps, and the coarsest solve is a dense inverse instead of an
 LU solve: both differences are rounding, amplified by at most the coarse
 levels' condition numbers, a few hundred here); the PCG's iteration count
 is within one of the oracle's and both meet the tolerance on the true
-residual."""
+residual.
+
+The mixed solve applies the same cycle in float (level matrices rounded
+to float once, float vectors) inside the FP64 outer CG with the
+Polak-Ribiere beta.  Its cycle agrees with the oracle's FP64 cycle within
+2e-5 relative to max |x| (float rounding, about 6e-8 per operation,
+amplified by the coarse levels' conditioning); the mixed PCG meets the
+same FP64 tolerance on the true residual, within two iterations of the
+oracle's count."""
 import numpy as np
 import pytest
 
@@ -81,6 +89,34 @@ def test_vcycle_matches_oracle(pkg, amg, name):
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
+def test_float_vcycle_matches_oracle(pkg, amg, name):
+    s = CASES[name]()
+    M = pkg.amg_from_system(s)
+    levels, coarse = amg.hierarchy(amg.csr_of(s))
+    rng = np.random.default_rng(8)
+    for b in (np.asarray(s.b, dtype=np.float64), rng.uniform(-1, 1, s.n)):
+        b32 = torch.as_tensor(b.astype(np.float32), device="cuda")
+        x = pkg.ldu_amg_vcycle(M, b32).cpu().numpy().astype(np.float64)
+        xo = amg.vcycle(levels, coarse, b.astype(np.float32).astype(np.float64))
+        err = np.max(np.abs(x - xo)) / np.max(np.abs(xo))
+        assert err <= 2e-5, err
+    M.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mixed_amg_pcg_meets_fp64_tolerance(pkg, amg, name):
+    s = CASES[name]()
+    M = pkg.amg_from_system(s)
+    r = amg.amg_pcg(s, tol=1e-8, maxit=200)
+    x, it, relres, st = pkg.amg_pcg_solve(M, dev(s.b), tol=1e-8, maxit=200, precision="mixed")
+    assert st == 0 and relres <= 1e-8
+    assert abs(it - r.iters) <= 2, (it, r.iters)
+    A = amg.csr_of(s)
+    assert np.linalg.norm(s.b - A @ x.cpu().numpy()) <= 1.0001e-8 * np.linalg.norm(s.b)
+    M.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
 def test_amg_pcg_matches_oracle(pkg, amg, name):
     s = CASES[name]()
     M = pkg.amg_from_system(s)
@@ -117,8 +153,10 @@ def test_small_system_is_the_coarsest_level(pkg, amg):
     x = pkg.ldu_amg_vcycle(M, dev(b)).cpu().numpy()
     xd = np.linalg.solve(amg.csr_of(s).toarray(), b)
     assert np.max(np.abs(x - xd)) <= 1e-12 * np.max(np.abs(xd))
-    _, it, relres, st = pkg.amg_pcg_solve(M, dev(b), tol=1e-10)
-    assert st == 0 and it == 1 and relres <= 1e-10
+    for precision in ("fp64", "mixed"):
+        _, it, relres, st = pkg.amg_pcg_solve(M, dev(b), tol=1e-10, precision=precision)
+        assert st == 0 and relres <= 1e-10
+        assert it == 1 if precision == "fp64" else it <= 2
     with pytest.raises(ValueError):
         pkg.ldu_amg_aggregates(M, 0)
     M.close()
@@ -144,6 +182,12 @@ def test_zero_rhs_and_bad_arguments(pkg):
     x0 = torch.ones(s.n, dtype=torch.float64, device="cuda")
     x, it, relres, st = pkg.amg_pcg_solve(M, torch.zeros_like(x0), x=x0)
     assert st == 0 and it == 0 and relres == 0.0 and float(x.abs().max()) == 0.0
+    x0 = torch.ones(s.n, dtype=torch.float64, device="cuda")
+    x, it, relres, st = pkg.amg_pcg_solve(M, torch.zeros_like(x0), x=x0, precision="mixed")
+    assert st == 0 and it == 0 and float(x.abs().max()) == 0.0
+    # maxit reached: NOT_CONVERGED with the iterate so far
+    x, it, relres, st = pkg.amg_pcg_solve(M, dev(s.b), tol=1e-14, maxit=2, check=False)
+    assert st == 1 and it == 2 and relres > 1e-14
     M.close()
     with pytest.raises(pkg.LduError):
         pkg.amg_from_system(s, max_coarse=5000)
@@ -163,7 +207,9 @@ def test_full_size_128_converges(pkg):
     info = M.info()
     assert info["rows"][0] == s.n and info["rows"][-1] <= 500
     assert all(a > b for a, b in zip(info["rows"], info["rows"][1:]))
-    x, it, relres, st = pkg.amg_pcg_solve(M, dev(s.b), tol=1e-8, maxit=200)
-    assert st == 0 and relres <= 1e-8
-    assert it <= 60   # Table 2 reports 32 for the paper's aggregation AMG at 128^3
+    for precision in ("fp64", "mixed"):
+        x, it, relres, st = pkg.amg_pcg_solve(M, dev(s.b), tol=1e-8, maxit=200,
+                                              precision=precision)
+        assert st == 0 and relres <= 1e-8
+        assert it <= 60   # Table 2 reports 32 for the paper's aggregation AMG at 128^3
     M.close()
