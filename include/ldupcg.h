@@ -366,8 +366,12 @@ int pcg_solve_batched(const ldu_matrix *A, const double *b, double *x, double to
 typedef struct ldu_amg ldu_amg;   /* opaque AMG hierarchy */
 
 typedef struct amg_opts {
-    int max_coarse;   /* coarsest-level rows at most this, 1..4096 (default 500) */
-    int max_levels;   /* prolongators at most this, 1..64 (default 12) */
+    int max_coarse;     /* coarsest-level rows at most this, 1..4096 (default 500) */
+    int max_levels;     /* prolongators at most this, 1..64 (default 12) */
+    int lanes_per_row;  /* lanes that share one row of R and of the coarse-level
+                           matrices: 1, 2, 4, 8, 16 or 32; 0 = the power of two
+                           nearest a quarter of the operator's mean row length
+                           (default) */
 } amg_opts;
 
 /* Build the hierarchy of an LDU matrix.  n, nFaces, owner, neighbour,

@@ -513,22 +513,22 @@ __global__ void __launch_bounds__(kThreads) k_amg_pre_csr(DCsr<T> A, const T *__
 }
 
 // post-smoothing: x = t + (w/d) (b - A t).  With DOT (level 0 inside the
-// outer PCG: b is the outer residual, x its preconditioned z) also
-// (r, z_new) and, with PR, (r, z_old) in FP64 from the double residual r64,
-// into the outer scalars
+// outer PCG: b is the outer residual in the cycle's precision, x its
+// preconditioned z) also (r, z_new) and, with PR, (r, z_old) into the outer
+// scalars: each thread sums its few rows in T, the grid in double (a float
+// cycle's dot products need no more: the float z carries 1e-7 already)
 template <typename T, bool DOT, bool PR>
 __global__ void __launch_bounds__(kThreads) k_amg_post(DSell<T> A, const T *__restrict__ d,
                                                        const T *__restrict__ wd,
                                                        const T *__restrict__ b,
                                                        const T *__restrict__ t,
                                                        T *__restrict__ x, const int *skip,
-                                                       const double *__restrict__ r64,
                                                        AmgScalars *S, double *part,
                                                        unsigned *count) {
     if (skip && *skip)
         return;
     const int lane = threadIdx.x & 31;
-    double dot = 0.0, doto = 0.0;
+    T dot = T(0), doto = T(0);   // this thread's rows (a handful), then FP64 across threads
     FOR_SLICES(A) {
         const int row = s * 32 + lane;
         const T off = sell_row(A, s, lane, [&](int c) { return t[c]; });
@@ -536,16 +536,15 @@ __global__ void __launch_bounds__(kThreads) k_amg_post(DSell<T> A, const T *__re
             const T bi = b[row], ti = t[row];
             const T xi = fma(wd[row], bi - fma(d[row], ti, off), ti);
             if (DOT) {
-                const double ri = r64[row];
                 if (PR)
-                    doto = fma(ri, (double)x[row], doto);
-                dot = fma(ri, (double)xi, dot);
+                    doto = fma(bi, x[row], doto);
+                dot = fma(bi, xi, dot);
             }
             x[row] = xi;
         }
     }
     if (DOT) {
-        double v[2] = {dot, doto}, tot[2];
+        double v[2] = {(double)dot, (double)doto}, tot[2];
         if (grid_sum_last<2>(v, part, count, tot) && threadIdx.x == 0)
             set_rz(S, tot[0], tot[1]);
     }
@@ -599,13 +598,12 @@ template <typename T, bool DOT, bool PR>
 __global__ void __launch_bounds__(kThreads) k_amg_dense(int n, const T *__restrict__ Minv,
                                                         const T *__restrict__ b,
                                                         T *__restrict__ x, const int *skip,
-                                                        const double *__restrict__ r64,
                                                         AmgScalars *S, double *part,
                                                         unsigned *count) {
     if (skip && *skip)
         return;
     const int lane = threadIdx.x & 31;
-    double dot = 0.0, doto = 0.0;
+    T dot = T(0), doto = T(0);
     for (int row = blockIdx.x * kWarps + (threadIdx.x >> 5); row < n; row += gridDim.x * kWarps) {
         T s = T(0);
         for (int k = lane; k < n; k += 32)
@@ -613,16 +611,15 @@ __global__ void __launch_bounds__(kThreads) k_amg_dense(int n, const T *__restri
         s = warp_sum(s);
         if (lane == 0) {
             if (DOT) {
-                const double ri = r64[row];
                 if (PR)
-                    doto = fma(ri, (double)x[row], doto);
-                dot = fma(ri, (double)s, dot);
+                    doto = fma(b[row], x[row], doto);
+                dot = fma(b[row], s, dot);
             }
             x[row] = s;
         }
     }
     if (DOT) {
-        double v[2] = {dot, doto}, tot[2];
+        double v[2] = {(double)dot, (double)doto}, tot[2];
         if (grid_sum_last<2>(v, part, count, tot) && threadIdx.x == 0)
             set_rz(S, tot[0], tot[1]);
     }
@@ -687,34 +684,34 @@ __global__ void __launch_bounds__(kThreads) k_amg_residual(DSell<double> A,
     }
 }
 
+// p = z + beta p, or p = z after a restart
 template <typename T>
-__device__ __forceinline__ double next_p(T z, double beta, double p, int restart) {
-    return restart ? (double)z : fma(beta, p, (double)z);
-}
-
-// p' = z + beta p (p' = z after a restart) and q = A p', p'_j formed on the
-// fly from z_j and p_j; (p', q) reduced into alpha
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_q(DSell<double> A, const double *__restrict__ d,
-                                                    const T *__restrict__ z,
-                                                    const double *__restrict__ p,
-                                                    double *__restrict__ pn,
-                                                    double *__restrict__ q, AmgScalars *S,
-                                                    double *part, unsigned *count) {
+__global__ void __launch_bounds__(kThreads) k_amg_p(int n, const T *__restrict__ z,
+                                                    double *__restrict__ p,
+                                                    const AmgScalars *S) {
     if (S->done)
         return;
     const int restart = S->restart;
     const double beta = S->beta;
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads)
+        p[i] = restart ? (double)z[i] : fma(beta, p[i], (double)z[i]);
+}
+
+// q = A p with (p, q) reduced into alpha
+__global__ void __launch_bounds__(kThreads) k_amg_q(DSell<double> A, const double *__restrict__ d,
+                                                    const double *__restrict__ p,
+                                                    double *__restrict__ q, AmgScalars *S,
+                                                    double *part, unsigned *count) {
+    if (S->done)
+        return;
     const int lane = threadIdx.x & 31;
     double pq = 0.0;
     FOR_SLICES(A) {
         const int row = s * 32 + lane;
-        const double off =
-            sell_row(A, s, lane, [&](int c) { return next_p(z[c], beta, p[c], restart); });
+        const double off = sell_row(A, s, lane, [&](int c) { return p[c]; });
         if (row < A.n) {
-            const double pi = next_p(z[row], beta, p[row], restart);
+            const double pi = p[row];
             const double qi = fma(d[row], pi, off);
-            pn[row] = pi;
             q[row] = qi;
             pq = fma(pi, qi, pq);
         }
@@ -939,7 +936,7 @@ struct ldu_amg {
     int64_t nc = 0, c_nnz = 0;      // coarsest rows and non-zeros
     CoarseVals<double> c64;         // coarsest dense inverse (row-major), vectors
     CoarseVals<float> c32;
-    double *r = nullptr, *z = nullptr, *p[2] = {nullptr, nullptr}, *q = nullptr;
+    double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     float *r32 = nullptr, *z32 = nullptr;   // float cycle's input and output
     double *part = nullptr;
     unsigned *count = nullptr;
@@ -980,8 +977,8 @@ void free_amg(ldu_amg *M) {
         free_vals(L.v32);
     }
     void *ptrs[] = {M->f_sp,   M->f_sw,   M->f_col,  M->f_val, M->f_d,    M->c64.inv, M->c64.x,
-                    M->c64.b,  M->c32.inv, M->c32.x, M->c32.b, M->r,      M->z,       M->p[0],
-                    M->p[1],   M->q,      M->r32,    M->z32,   M->part,   M->count,   M->S};
+                    M->c64.b,  M->c32.inv, M->c32.x, M->c32.b, M->r,      M->z,       M->p,
+                    M->q,      M->r32,    M->z32,   M->part,   M->count,   M->S};
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
@@ -996,19 +993,16 @@ void free_amg(ldu_amg *M) {
 // the double residual r64 (PR: the flexible-CG beta).
 template <typename T>
 int vcycle(ldu_amg *M, size_t l, const T *b, T *x, bool dot, const int *skip, cudaStream_t st) {
-    const bool pr = std::is_same<T, float>::value;
+    constexpr bool pr = std::is_same<T, float>::value;
     if (l == M->lev.size()) {
         const CoarseVals<T> &C = M->c<T>();
         const int g = grid_warps(M->nc);
         if (!dot)
-            k_amg_dense<T, false, false><<<g, kThreads, 0, st>>>(
-                (int)M->nc, C.inv, b, x, skip, nullptr, nullptr, nullptr, nullptr);
-        else if (pr)
-            k_amg_dense<T, true, true><<<g, kThreads, 0, st>>>((int)M->nc, C.inv, b, x, skip, M->r,
-                                                               M->S, M->part, M->count);
+            k_amg_dense<T, false, false><<<g, kThreads, 0, st>>>((int)M->nc, C.inv, b, x, skip,
+                                                                 nullptr, nullptr, nullptr);
         else
-            k_amg_dense<T, true, false><<<g, kThreads, 0, st>>>((int)M->nc, C.inv, b, x, skip,
-                                                                M->r, M->S, M->part, M->count);
+            k_amg_dense<T, true, pr><<<g, kThreads, 0, st>>>((int)M->nc, C.inv, b, x, skip, M->S,
+                                                             M->part, M->count);
         return cuda_status(cudaGetLastError());
     }
     const amg_level &L = M->lev[l];
@@ -1032,14 +1026,11 @@ int vcycle(ldu_amg *M, size_t l, const T *b, T *x, bool dot, const int *skip, cu
     if (l == 0) {
         const int g = grid_rows(L.n);
         if (!dot)
-            k_amg_post<T, false, false><<<g, kThreads, 0, st>>>(
-                L.A<T>(), V.d, V.wd, b, V.t, x, skip, nullptr, nullptr, nullptr, nullptr);
-        else if (pr)
-            k_amg_post<T, true, true><<<g, kThreads, 0, st>>>(L.A<T>(), V.d, V.wd, b, V.t, x, skip,
-                                                              M->r, M->S, M->part, M->count);
+            k_amg_post<T, false, false><<<g, kThreads, 0, st>>>(L.A<T>(), V.d, V.wd, b, V.t, x,
+                                                                skip, nullptr, nullptr, nullptr);
         else
-            k_amg_post<T, true, false><<<g, kThreads, 0, st>>>(
-                L.A<T>(), V.d, V.wd, b, V.t, x, skip, M->r, M->S, M->part, M->count);
+            k_amg_post<T, true, pr><<<g, kThreads, 0, st>>>(L.A<T>(), V.d, V.wd, b, V.t, x, skip,
+                                                            M->S, M->part, M->count);
     } else {
         launch_post_csr<T>(L.a_lpr, grid_lpr(L.n, L.a_lpr), st, L.Acsr<T>(), (const T *)V.d,
                            (const T *)V.wd, b, (const T *)V.t, x, skip);
@@ -1086,7 +1077,7 @@ int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int 
         return rc;
     if ((rc = read_scalars(M, st)) != LDU_OK)
         return rc;
-    int status = LDU_NOT_CONVERGED, it = 0, cur = 0;
+    int status = LDU_NOT_CONVERGED, it = 0;
     bool confirmed = false;   // H->rr holds the true residual of the final x
     const double bn2 = H->bn2, thr2 = H->thr2;
     if (bn2 == 0.0) {
@@ -1102,11 +1093,10 @@ int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int 
         int it_prev = 0, batch = 4;
         for (;;) {
             for (int g = 0; g < batch; ++g) {
-                k_amg_q<T><<<ga, kThreads, 0, st>>>(A, d, (const T *)cyc_z, M->p[cur],
-                                                    M->p[cur ^ 1], M->q, S, M->part, M->count);
-                cur ^= 1;
-                k_amg_xr<T><<<ga, kThreads, 0, st>>>((int)n, M->p[cur], M->q, x, M->r, wd0, t0,
-                                                     bv, S, M->part, M->count);
+                k_amg_p<T><<<ga, kThreads, 0, st>>>((int)n, (const T *)cyc_z, M->p, S);
+                k_amg_q<<<ga, kThreads, 0, st>>>(A, d, M->p, M->q, S, M->part, M->count);
+                k_amg_xr<T><<<ga, kThreads, 0, st>>>((int)n, M->p, M->q, x, M->r, wd0, t0, bv, S,
+                                                     M->part, M->count);
                 if ((rc = vcycle<T>(M, 0, cyc_b, cyc_z, true, &S->done, st)) != LDU_OK)
                     return rc;
             }
@@ -1176,14 +1166,16 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
     *out = nullptr;
     if (n <= 0 || nf < 0 || !diag || (nf > 0 && (!owner || !neighbour || !upper || !lower)))
         return LDU_ERR_BAD_ARG;
-    int max_coarse = 500, max_levels = 12;
+    int max_coarse = 500, max_levels = 12, lanes = 0;
     if (aopt) {
         if (aopt->max_coarse)
             max_coarse = aopt->max_coarse;
         if (aopt->max_levels)
             max_levels = aopt->max_levels;
+        lanes = aopt->lanes_per_row;
     }
-    if (max_coarse < 1 || max_coarse > kMaxCoarse || max_levels < 1 || max_levels > 64)
+    if (max_coarse < 1 || max_coarse > kMaxCoarse || max_levels < 1 || max_levels > 64 ||
+        lanes < 0 || lanes > 32 || (lanes & (lanes - 1)) != 0)
         return LDU_ERR_BAD_ARG;
     if (n > INT32_MAX / 2 || nf > INT32_MAX / 2)
         return LDU_ERR_UNSUPPORTED;
@@ -1279,13 +1271,13 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
                     }
                 ap[(size_t)i + 1] = (int)ac.size();
             }
-            L.a_lpr = lpr_for(A.n, (int64_t)ac.size());
+            L.a_lpr = lanes ? lanes : lpr_for(A.n, (int64_t)ac.size());
             CKA(upload(&L.a_ptr, ap, nb));
             CKA(upload(&L.a_col, ac, nb));
             CKA(upload2(&L.v64.a_val, &L.v32.a_val, av, nb));
         }
         L.p_lpr = lpr_for(P.n, (int64_t)P.col.size());
-        L.r_lpr = lpr_for(R.n, (int64_t)R.col.size());
+        L.r_lpr = lanes ? lanes : lpr_for(R.n, (int64_t)R.col.size());
         L.r_rows = R.n;
         std::vector<int> pp(P.ptr.begin(), P.ptr.end()), rp(R.ptr.begin(), R.ptr.end());
         CKA(upload2(&L.v64.d, &L.v32.d, d, nb));
@@ -1343,8 +1335,7 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
     CKA(alloc(&M->c32.b, A.n, nb));
     CKA(alloc(&M->r, n, nb));
     CKA(alloc(&M->z, n, nb));
-    CKA(alloc(&M->p[0], n, nb));
-    CKA(alloc(&M->p[1], n, nb));
+    CKA(alloc(&M->p, n, nb));
     CKA(alloc(&M->q, n, nb));
     CKA(alloc(&M->r32, n, nb));
     CKA(alloc(&M->z32, n, nb));

@@ -44,7 +44,8 @@ class BatchOpts(ctypes.Structure):
 
 
 class AmgOpts(ctypes.Structure):
-    _fields_ = [("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int)]
+    _fields_ = [("max_coarse", ctypes.c_int), ("max_levels", ctypes.c_int),
+                ("lanes_per_row", ctypes.c_int)]
 
 
 class LduSolveStats(ctypes.Structure):
@@ -428,14 +429,14 @@ class LduAmg:
 
 
 def ldu_amg_create(n, owner, neighbour, diag, upper, lower, max_coarse=0, max_levels=0,
-                   stream=None):
+                   lanes_per_row=0, stream=None):
     """Build the AMG hierarchy of an LDU matrix given as device tensors."""
     nf = owner.numel()
     args = [ctypes.c_int64(n), ctypes.c_int64(nf),
             _dev(owner, torch.int32, nf, "owner"), _dev(neighbour, torch.int32, nf, "neighbour"),
             _dev(diag, torch.float64, n, "diag"), _dev(upper, torch.float64, nf, "upper"),
             _dev(lower, torch.float64, nf, "lower")]
-    aopts = AmgOpts(max_coarse, max_levels)
+    aopts = AmgOpts(max_coarse, max_levels, lanes_per_row)
     h = _vp()
     st = lib().ldu_amg_create(*args, ctypes.byref(aopts), _stream(stream), ctypes.byref(h))
     _check(st, "ldu_amg_create", allow_not_converged=False)

@@ -145,7 +145,8 @@ def test_amg_pcg_nonzero_initial_guess(pkg, amg):
 
 def test_small_system_is_the_coarsest_level(pkg, amg):
     """n <= max_coarse: no prolongator, the V-cycle is the exact inverse and
-    PCG converges in one iteration."""
+    PCG converges in one iteration (the float inverse of the mixed solve
+    gains about 1e-6 a step, so a few)."""
     s = lc.poisson_box(7, 6, 5, diffusivity="lognormal", seed=2)
     M = pkg.amg_from_system(s)
     assert M.info() == {"levels": 1, "rows": [s.n], "nnz": [s.n + 2 * len(s.owner)]}
@@ -156,7 +157,7 @@ def test_small_system_is_the_coarsest_level(pkg, amg):
     for precision in ("fp64", "mixed"):
         _, it, relres, st = pkg.amg_pcg_solve(M, dev(b), tol=1e-10, precision=precision)
         assert st == 0 and relres <= 1e-10
-        assert it == 1 if precision == "fp64" else it <= 2
+        assert it == 1 if precision == "fp64" else it <= 4
     with pytest.raises(ValueError):
         pkg.ldu_amg_aggregates(M, 0)
     M.close()
@@ -176,6 +177,20 @@ def test_max_levels_and_max_coarse(pkg, amg):
         M.close()
 
 
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+def test_lanes_per_row_keeps_the_cycle(pkg, amg, lanes):
+    """The lanes sharing a row of R and of the coarse matrices only change
+    the order of each row's sum."""
+    s = CASES["lognormal_rcm24"]()
+    M = pkg.amg_from_system(s, lanes_per_row=lanes)
+    levels, coarse = amg.hierarchy(amg.csr_of(s))
+    b = np.random.default_rng(9).uniform(-1, 1, s.n)
+    x = pkg.ldu_amg_vcycle(M, dev(b)).cpu().numpy()
+    xo = amg.vcycle(levels, coarse, b)
+    assert np.max(np.abs(x - xo)) <= 1e-11 * np.max(np.abs(xo))
+    M.close()
+
+
 def test_zero_rhs_and_bad_arguments(pkg):
     s = lc.poisson_box(12)
     M = pkg.amg_from_system(s)
@@ -193,6 +208,8 @@ def test_zero_rhs_and_bad_arguments(pkg):
         pkg.amg_from_system(s, max_coarse=5000)
     with pytest.raises(pkg.LduError):
         pkg.amg_from_system(s, max_levels=-1)
+    with pytest.raises(pkg.LduError):
+        pkg.amg_from_system(s, lanes_per_row=3)
     # coarsening stopped above the dense-inverse limit
     with pytest.raises(pkg.LduError) as e:
         pkg.amg_from_system(lc.poisson_box(48), max_levels=1)
