@@ -536,8 +536,9 @@ def run_batched(args, dev, pkg, timed_fn):
 
 def run_amg(args, dev, pkg, s, timed_fn):
     """Aggregation-AMG preconditioned CG (Sec. 5, Table 2's AMG-CG) on the
-    headline system, FP64, to 1e-8: hierarchy setup (host, once per matrix),
-    one V-cycle, and the whole solve."""
+    headline system to 1e-8: hierarchy setup (host, once per matrix), one
+    V-cycle in each precision, and the whole solve with the FP64 cycle and
+    with the float cycle inside the FP64 outer CG."""
     import time
 
     import torch
@@ -549,21 +550,23 @@ def run_amg(args, dev, pkg, s, timed_fn):
     b = torch.as_tensor(s.b, device=dev)
     x = torch.zeros_like(b)
     z = torch.empty_like(b)
-    res = {}
+    b32 = b.float()
+    z32 = torch.empty_like(b32)
+    out = {"setup_s": setup_s, "levels": M.info()["rows"]}
+    for name, bb, zz in (("vcycle_fp64_ms", b, z), ("vcycle_fp32_ms", b32, z32)):
+        def cycles(bb=bb, zz=zz):
+            for _ in range(10):
+                pkg.ldu_amg_vcycle(M, bb, zz)
+        out[name] = statistics.median(timed_fn(cycles, 3, 1)) * 100.0
+    for prec in ("mixed", "fp64"):
+        res = {}
 
-    def solve():
-        res["out"] = pkg.amg_pcg_solve(M, b, x, tol=TOL, maxit=500)
+        def solve(prec=prec, res=res):
+            res["out"] = pkg.amg_pcg_solve(M, b, x, tol=TOL, maxit=500, precision=prec)
 
-    def cycles():
-        for _ in range(10):
-            pkg.ldu_amg_vcycle(M, b, z)
-
-    t = timed_fn(solve, 2, 1, prep=x.zero_)
-    tv = timed_fn(cycles, 2, 1)
-    _, it, rr, st = res["out"]
-    out = {"s": statistics.median(t), "iters": it, "relres": rr, "status": st,
-           "setup_s": setup_s, "vcycle_ms": statistics.median(tv) * 100.0,
-           "levels": M.info()["rows"]}
+        t = timed_fn(solve, 3, 1, prep=x.zero_)
+        _, it, rr, st = res["out"]
+        out[prec] = {"s": statistics.median(t), "iters": it, "relres": rr, "status": st}
     M.close()
     return out
 

@@ -36,6 +36,12 @@ namespace {
 
 constexpr double kTie = 1e-12;
 constexpr int kMaxCoarse = 4096;   // largest coarsest level (dense inverse: 128 MiB)
+// a coarse level's A goes to sliced ELL when its padded slots are at most
+// this multiple of its off-diagonal entries, else to CSR.  Measured on the
+// 128^3 hierarchy in float: the 263k-row level (30 entries a row, 29 %
+// padding) in sliced ELL made the cycle 12 % slower than CSR with 8 lanes a
+// row, so only an unpadded coarse level would take it.
+constexpr double kSellPad = 1.0;
 
 // ---- host sparse matrices ----------------------------------------------------
 
@@ -901,6 +907,7 @@ struct amg_level {
     int *p_ptr = nullptr, *p_col = nullptr;   // P: n x n_next
     int *r_ptr = nullptr, *r_col = nullptr;   // R = P^T: n_next x n
     int a_lpr = 1, p_lpr = 1, r_lpr = 1;      // lanes per row of the CSR reads
+    bool a_sell = false;                      // A in sliced ELL (else CSR)
     int64_t r_rows = 0;                       // rows of R (= next level's)
     LevelVals<double> v64;
     LevelVals<float> v32;
@@ -1007,7 +1014,7 @@ int vcycle(ldu_amg *M, size_t l, const T *b, T *x, bool dot, const int *skip, cu
     }
     const amg_level &L = M->lev[l];
     const LevelVals<T> &V = L.v<T>();
-    if (l == 0)
+    if (L.a_sell)
         k_amg_pre<T><<<grid_rows(L.n), kThreads, 0, st>>>(L.A<T>(), V.d, b, V.t, V.r, skip);
     else
         launch_pre_csr<T>(L.a_lpr, grid_lpr(L.n, L.a_lpr), st, L.Acsr<T>(), (const T *)V.d, b,
@@ -1023,7 +1030,7 @@ int vcycle(ldu_amg *M, size_t l, const T *b, T *x, bool dot, const int *skip, cu
     if (rc != LDU_OK)
         return rc;
     launch_prolong<T>(L.p_lpr, grid_lpr(L.n, L.p_lpr), st, L.P<T>(), (const T *)xn, V.t, skip);
-    if (l == 0) {
+    if (L.a_sell) {
         const int g = grid_rows(L.n);
         if (!dot)
             k_amg_post<T, false, false><<<g, kThreads, 0, st>>>(L.A<T>(), V.d, V.wd, b, V.t, x,
@@ -1247,12 +1254,14 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
             d[(size_t)i] = diag_of(A, i);
             wd[(size_t)i] = L.w / d[(size_t)i];
         }
-        if (M->lev.size() == 1) {
-            HSell S;
-            if (!sell_of(A, S)) {
-                free_amg(M);
-                return LDU_ERR_UNSUPPORTED;
-            }
+        HSell S;
+        if (!sell_of(A, S)) {
+            free_amg(M);
+            return LDU_ERR_UNSUPPORTED;
+        }
+        const int64_t off_nnz = (int64_t)A.col.size() - A.n;
+        L.a_sell = M->lev.size() == 1 || (double)S.sp.back() <= kSellPad * (double)off_nnz;
+        if (L.a_sell) {
             CKA(upload(&L.a_sp, S.sp, nb));
             CKA(upload(&L.a_sw, S.sw, nb));
             CKA(upload(&L.a_col, S.col, nb));
