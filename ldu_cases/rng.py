@@ -24,6 +24,8 @@ TAGS = {
     "sides": 6,
     "ref_diffusivity": 7,
     "probe": 8,
+    "piso-flux": 9,
+    "piso-dflux": 10,
 }
 
 
