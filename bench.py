@@ -423,9 +423,10 @@ def run_ours(args):
     batched = None
     if not args.skip_batched:
         batched = run_batched(args, dev, pkg, timed_fn=timed_generic)
-    pressure = autograd_case = heat = amg_case = None
+    pressure = autograd_case = heat = amg_case = piso_case = None
     if not args.skip_extra:
         amg_case = run_amg(args, dev, pkg, s, timed_fn=timed_generic)
+        piso_case = run_piso(args, dev, pkg, timed_fn=timed_generic)
         pressure = run_pressure(args, dev, pkg, timed_fn=timed_generic)
         autograd_case = run_autograd(args, dev, pkg, timed_fn=timed_generic)
         heat = run_heat(args, dev, pkg, timed_fn=timed_generic)
@@ -473,6 +474,7 @@ def run_ours(args):
         "differentiable": autograd_case,
         "heat_steps": heat,
         "amg_pcg": amg_case,
+        "piso_pressure": piso_case,
     }
     line.update(extra)
     emit(line, ranks)
@@ -637,6 +639,45 @@ def run_heat(args, dev, pkg, timed_fn):
     A.close()
     return {"cells": s.n, "steps": 10, "dt_over_h2": 1.0, "s_per_step": statistics.median(t) / 10,
             "iterations_per_step": out["iterations"] / 10, "relres_last": out["relres_last"],
+            "status": out["status"]}
+
+
+def run_piso(args, dev, pkg, timed_fn):
+    """icoFoam-style pressure stages (Sec. 2's PISO): 10 time steps on the
+    graded 128³ pressure system (pure Neumann with a pinned cell), predicted
+    fluxes phi*_k = phi_0 + 1e-3 k dphi, each step b = -div(phi*), a mixed
+    deflated solve to 1e-8 warm-started from the previous pressure, and the
+    flux correction, on one handle."""
+    import torch
+
+    import ldu_cases as lc
+    from ldu_cases import rng
+
+    s = lc.config3(s=args.size, seed=0)
+    A = pkg.from_system(s, device=dev, slice_rows=128)
+    coef = torch.as_tensor(s.coef, device=dev)
+    phi0 = torch.as_tensor(rng.uniform(rng.stream_base(0, "piso-flux"), s.nfaces, -1.0, 1.0),
+                           device=dev)
+    dphi = torch.as_tensor(rng.uniform(rng.stream_base(0, "piso-dflux"), s.nfaces, -1.0, 1.0),
+                           device=dev)
+    phi = torch.empty_like(phi0)
+    p = torch.zeros(s.n, dtype=torch.float64, device=dev)
+    out = {"iters": 0}
+
+    def steps():
+        p.zero_()
+        out["iters"] = 0
+        for k in range(10):
+            torch.add(phi0, dphi, alpha=1e-3 * k, out=phi)
+            st, it, rr = pkg.ldu_piso_pressure(A, coef, phi, p, tol=TOL, precision="mixed",
+                                               deflate=True)
+            out["iters"] += it
+            out["status"], out["relres"] = st, rr
+
+    t = timed_fn(steps, 2, 1)
+    A.close()
+    return {"cells": s.n, "faces": s.nfaces, "steps": 10, "s_per_step": statistics.median(t) / 10,
+            "iterations_per_step": out["iters"] / 10, "relres_last": out["relres"],
             "status": out["status"]}
 
 

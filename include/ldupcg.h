@@ -338,6 +338,31 @@ int pcg_solve_batched(const ldu_matrix *A, const double *b, double *x, double to
                       int precision, const pcg_opts *opts, int *iters, double *relres,
                       int *status, ldu_stream_t stream);
 
+/* The pressure stage of a PISO step (Sec. 2, icoFoam: the pressure solution
+ * and the explicit correction after the momentum predictor), on a handle
+ * whose matrix is the pressure matrix of the face coefficients `coef`
+ * (upper = lower = -coef, diagonal = the coefficient sums plus the
+ * reference-cell pin, e.g. set by ldu_set_face_coeffs):
+ *   1. b = -div(phi), div_P = sum of phi_f over the faces P owns minus the
+ *      sum over the faces where P is the neighbour (formed per cell in the
+ *      order of its neighbours, so repeated calls agree bitwise);
+ *   2. A p = b solved from the caller's p (the previous pressure: a warm
+ *      start), with pcg_solve (LDU_FP64) or the mixed pipelined method
+ *      (LDU_MIXED; opts as pipecg_solve, e.g. deflate for pure-Neumann
+ *      pressure systems);
+ *   3. phi_f -= coef_f (p[neighbour[f]] - p[owner[f]]), after which
+ *      div(phi) equals the solve's residual (zero to its tolerance).
+ *   coef   device double[nFaces]
+ *   phi    device double[nFaces]: the predicted fluxes in, corrected out
+ *   p      device double[n]: initial guess in, pressure out
+ *   iters, relres: host, may be NULL (the solve's counts).
+ * Single-system handles only (UNSUPPORTED on a batch).  On NOT_CONVERGED
+ * the fluxes are corrected with the last iterate; on an error phi is left
+ * as it was.  Synchronises stream. */
+int ldu_piso_pressure(ldu_matrix *A, const double *coef, double *phi, double *p, double tol,
+                      int maxit, int precision, const pcg_opts *opts, int *iters,
+                      double *relres, ldu_stream_t stream);
+
 /* ---- aggregation-AMG preconditioned CG (Sec. 5; Table 2's AMG-CG) ----
  *
  * The paper also preconditions CG with a V-cycle of an aggregation-based

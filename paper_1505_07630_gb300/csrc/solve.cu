@@ -47,6 +47,37 @@ __global__ void k_mass_rhs(int64_t n, const double *__restrict__ mass,
         b[i] = mass[i] * T[i];
 }
 
+// b = -div(phi) for the pressure stage of a PISO step: row r (a cell) adds
+// +phi_f over the faces where it is the neighbour (the slot holds the lower
+// coefficient) and -phi_f over the faces it owns, in its slot order (the
+// order of its neighbours), so that repeated calls agree bitwise
+__global__ void k_neg_div(int n, int C, const int *__restrict__ slice_ptr,
+                          const int *__restrict__ slice_w, const uint32_t *__restrict__ fid,
+                          const double *__restrict__ phi, double *__restrict__ b) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int s = r / C, i = r - s * C;
+        const int base = slice_ptr[s] + i, w = slice_w[s];
+        double acc = 0.0;
+        for (int q = 0; q < w; ++q) {
+            const uint32_t f = fid[base + q * C];
+            if (f == kPadFid)
+                continue;
+            const double v = phi[f & ~kLowerBit];
+            acc += (f & kLowerBit) ? v : -v;
+        }
+        b[r] = acc;
+    }
+}
+
+// phi_f -= c_f (p_N - p_P), P the owner and N the neighbour of face f
+__global__ void k_flux_correct(int64_t nf, const int32_t *__restrict__ own,
+                               const int32_t *__restrict__ nbr, const double *__restrict__ coef,
+                               const double *__restrict__ p, double *__restrict__ phi) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+         f += (int64_t)gridDim.x * blockDim.x)
+        phi[f] = fma(-coef[f], p[nbr[f]] - p[own[f]], phi[f]);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 
@@ -306,6 +337,49 @@ int ldu_heat_steps(ldu_matrix *A, const double *mass, double *T, int nsteps, dou
         *iters_total = total;
     if (relres_last)
         *relres_last = rr;
+    return rc;
+}
+
+int ldu_piso_pressure(ldu_matrix *A, const double *coef, double *phi, double *p, double tol,
+                      int maxit, int precision, const pcg_opts *opts, int *iters,
+                      double *relres, ldu_stream_t stream) {
+    if (!A || (A->n > 0 && !p) || (A->nf > 0 && (!coef || !phi)) ||
+        (precision != LDU_FP64 && precision != LDU_MIXED))
+        return LDU_ERR_BAD_ARG;
+    if (A->row_cell)
+        return LDU_ERR_UNSUPPORTED;   // single-system handles only
+    cudaStream_t st = (cudaStream_t)stream;
+    if (iters)
+        *iters = 0;
+    if (relres)
+        *relres = 0.0;
+    if (A->n == 0)
+        return LDU_OK;
+    if (!A->rhs) {
+        cudaError_t e = cudaMalloc((void **)&A->rhs, sizeof(double) * (size_t)A->n);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+        A->device_bytes += (int64_t)sizeof(double) * A->n;
+    }
+    const int grid_n = (int)std::min<int64_t>((A->n + 255) / 256, 1 << 20);
+    k_neg_div<<<grid_n, 256, 0, st>>>((int)A->n, A->C, A->slice_ptr, A->slice_w, A->fid, phi,
+                                      A->rhs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    const int rc = run_solver(A, precision == LDU_FP64 ? kPcg : kMixed, A->rhs, p, tol, maxit,
+                              opts, iters, relres, st);
+    if (rc != LDU_OK && rc != LDU_NOT_CONVERGED)
+        return rc;
+    if (A->nf > 0) {
+        k_flux_correct<<<(int)std::min<int64_t>((A->nf + 255) / 256, 1 << 20), 256, 0, st>>>(
+            A->nf, A->owner, A->neighbour, coef, p, phi);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+    }
     return rc;
 }
 

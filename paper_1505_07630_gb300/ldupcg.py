@@ -100,6 +100,9 @@ def lib():
         L.ldu_heat_steps.argtypes = [_vp, _vp, _vp, i, d, i, i, ctypes.POINTER(PcgOpts), pi, pd,
                                      _vp]
         L.ldu_heat_steps.restype = i
+        L.ldu_piso_pressure.argtypes = [_vp, _vp, _vp, _vp, d, i, i, ctypes.POINTER(PcgOpts), pi,
+                                        pd, _vp]
+        L.ldu_piso_pressure.restype = i
         L.ldu_harmonic_coeffs.argtypes = [_vp] * 7
         L.ldu_harmonic_coeffs.restype = i
         L.ldu_harmonic_grad.argtypes = [_vp] * 8
@@ -342,6 +345,25 @@ def ldu_heat_steps(A, mass, T, nsteps, tol=1e-8, maxit=20000, precision="mixed",
     if check:
         _check(st, "ldu_heat_steps")
     return T, st, it.value, rr.value
+
+
+def ldu_piso_pressure(A, coef, phi, p, tol=1e-8, maxit=20000, precision="mixed", rr_period=0,
+                      tau=0.0, deflate=False, stream=None, check=True):
+    """Pressure stage of a PISO step: b = -div(phi), solve A p = b from p,
+    phi -= coef (p_N - p_P).  phi and p are updated in place; returns
+    (status, iters, relres)."""
+    prec = {"fp64": FP64, "mixed": MIXED}[precision]
+    opts = PcgOpts(rr_period=rr_period, tau=tau, deflate=int(bool(deflate)))
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().ldu_piso_pressure(A.handle, _dev(coef, torch.float64, A.nfaces, "coef"),
+                                 _dev(phi, torch.float64, A.nfaces, "phi"),
+                                 _dev(p, torch.float64, A.n, "p"), float(tol), int(maxit), prec,
+                                 ctypes.byref(opts), ctypes.byref(it), ctypes.byref(rr),
+                                 _stream(stream))
+    if check:
+        _check(st, "ldu_piso_pressure")
+    return st, it.value, rr.value
 
 
 def ldu_harmonic_coeffs(A, k, g, bfac, coef=None, extra=None, stream=None):
