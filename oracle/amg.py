@@ -26,7 +26,8 @@ around a distance-2 maximal independent set, with weighted Jacobi
   most `max_coarse` rows, which is solved exactly;
 * V(1,1) cycle with the same weighted Jacobi as smoother, started from zero;
 * PCG (Saad Alg. 9.1) with z = V(r), stopping on the recursive ||r||/||b||
-  and confirming with the true residual, as the Jacobi oracle does.
+  and confirming with the true residual, as the Jacobi oracle does;
+* the pipelined form of the same PCG (Table 2's AMG-PipeCG), `amg_pipecg`.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -168,5 +169,65 @@ def amg_pcg(s, b=None, tol=1e-8, maxit=500, max_coarse=500):
         rz_new = r @ z
         p = z + (rz_new / rz) * p
         rz = rz_new
+    relres = np.linalg.norm(b - A @ x) / bn
+    return Result(x, it, relres, len(levels) + 1)
+
+
+def amg_pipecg(s, b=None, tol=1e-8, maxit=500, max_coarse=500):
+    """Pipelined PCG (Ghysels & Vanroose 2014, the preconditioned variant the
+    paper's Sec. 4.1 builds on) with M = the V-cycle: one cycle and one
+    product per iteration and the three dot products (r, u), (w, u), (r, r)
+    of a step formed together.  Recurrences: u = M r, w = A u, m = M w,
+    n = A m; z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p;
+    x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z.  Stops on the
+    recursive ||r|| and confirms with the true residual (a disagreement
+    restarts the recurrences from it)."""
+    A = csr_of(s)
+    b = np.asarray(s.b if b is None else b, dtype=np.float64)
+    levels, coarse = hierarchy(A, max_coarse)
+    bn = np.linalg.norm(b)
+    x = np.zeros(s.n)
+    if bn == 0.0:
+        return Result(x, 0, 0.0, len(levels) + 1)
+    r = b.copy()
+    it = 0
+    while True:
+        # (re)start of the recurrences from the current residual
+        u = vcycle(levels, coarse, r)
+        w = A @ u
+        z = np.zeros(s.n)
+        q = np.zeros(s.n)
+        sv = np.zeros(s.n)
+        p = np.zeros(s.n)
+        gamma_old = alpha_old = None
+        gamma, delta = r @ u, w @ u
+        converged = False
+        while it < maxit:
+            m = vcycle(levels, coarse, w)
+            nv = A @ m
+            if gamma_old is None:
+                beta, alpha = 0.0, gamma / delta
+            else:
+                beta = gamma / gamma_old
+                alpha = gamma / (delta - beta * gamma / alpha_old)
+            z = nv + beta * z
+            q = m + beta * q
+            sv = w + beta * sv
+            p = u + beta * p
+            x = x + alpha * p
+            r = r - alpha * sv
+            u = u - alpha * q
+            w = w - alpha * z
+            it += 1
+            gamma_old, alpha_old = gamma, alpha
+            gamma, delta = r @ u, w @ u
+            if np.linalg.norm(r) <= tol * bn:
+                converged = True
+                break
+        if not converged:
+            break
+        r = b - A @ x
+        if np.linalg.norm(r) <= tol * bn or it >= maxit:
+            break
     relres = np.linalg.norm(b - A @ x) / bn
     return Result(x, it, relres, len(levels) + 1)

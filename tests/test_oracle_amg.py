@@ -108,3 +108,36 @@ def test_table2_amg_magnitude():
     r = amg.amg_pcg(lc.config1(s=64), tol=1e-8)
     assert r.relres <= 1e-8
     assert 0.5 * ref <= r.iters <= 2 * ref, r.iters
+
+
+def test_pipelined_amg_pcg_matches_plain_and_dense():
+    """In exact arithmetic pipelined PCG produces PCG's iterates; Table 2
+    reports the same iteration counts for the paper's AMG-CG and AMG-PipeCG
+    (28 and 32 both).  Here: the same count within one, and the dense
+    solution."""
+    s = lc.poisson_box(10, 9, 8, diffusivity="lognormal", seed=6)
+    r1 = amg.amg_pcg(s, tol=1e-10)
+    r2 = amg.amg_pipecg(s, tol=1e-10)
+    assert abs(r1.iters - r2.iters) <= 1
+    assert r2.relres <= 1e-10
+    xd = np.linalg.solve(amg.csr_of(s).toarray(), s.b)
+    assert np.max(np.abs(r2.x - xd)) <= 1e-8 * np.max(np.abs(xd))
+
+
+def test_pipelined_amg_pcg_larger_and_zero_rhs():
+    s = lc.poisson_box(24, diffusivity="lognormal", seed=1)
+    r1 = amg.amg_pcg(s, tol=1e-8)
+    r2 = amg.amg_pipecg(s, tol=1e-8)
+    assert abs(r1.iters - r2.iters) <= 1 and r2.relres <= 1e-8
+    z = amg.amg_pipecg(s, b=np.zeros(s.n))
+    assert z.iters == 0 and np.all(z.x == 0.0)
+
+
+def test_pipelined_iterates_equal_pcg_iterates():
+    """Pipelined PCG is PCG reorganised: after k steps both hold the same
+    iterate (up to rounding), whatever k."""
+    s = lc.poisson_box(9, 8, 7, diffusivity="lognormal", seed=4)
+    for k in (1, 3, 6):
+        x1 = amg.amg_pcg(s, tol=1e-30, maxit=k).x
+        x2 = amg.amg_pipecg(s, tol=1e-30, maxit=k).x
+        assert np.max(np.abs(x1 - x2)) <= 1e-10 * np.max(np.abs(x1)), k
