@@ -560,11 +560,14 @@ def run_amg(args, dev, pkg, s, timed_fn):
             for _ in range(10):
                 pkg.ldu_amg_vcycle(M, bb, zz)
         out[name] = statistics.median(timed_fn(cycles, 3, 1)) * 100.0
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp64", "pipelined_fp64"):
         res = {}
 
         def solve(prec=prec, res=res):
-            res["out"] = pkg.amg_pcg_solve(M, b, x, tol=TOL, maxit=500, precision=prec)
+            if prec == "pipelined_fp64":
+                res["out"] = pkg.amg_pipecg_solve(M, b, x, tol=TOL, maxit=500)
+            else:
+                res["out"] = pkg.amg_pcg_solve(M, b, x, tol=TOL, maxit=500, precision=prec)
 
         t = timed_fn(solve, 3, 1, prep=x.zero_)
         _, it, rr, st = res["out"]

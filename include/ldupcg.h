@@ -444,6 +444,18 @@ int ldu_amg_vcycle(ldu_amg *M, int precision, const void *b, void *x, ldu_stream
 int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int precision,
                   int *iters, double *relres, ldu_stream_t stream);
 
+/* Pipelined AMG-preconditioned CG (Table 2's AMG-PipeCG; Ghysels & Vanroose's
+ * pipelined PCG, the method of Sec. 4.1, with M = one FP64 V-cycle): per
+ * iteration one cycle m = V(w), one product n = A m, and one pass that
+ * updates z, q, s, p, x, r, u, w and forms (r, u), (w, u), (r, r) together.
+ * In exact arithmetic its iterates are amg_pcg_solve's.  Stops on the
+ * recursive residual and confirms with the true one (a disagreement
+ * restarts the recurrences from it).  Arguments, outputs and errors as
+ * amg_pcg_solve (FP64 only).  Allocates seven work vectors on a hierarchy's
+ * first call.  Synchronises stream. */
+int amg_pipecg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
+                     double *relres, ldu_stream_t stream);
+
 /* Jacobi-PCG on a small LDU system without any device allocation.  The paper
  * has no counterpart: this exists for callers that cannot call cudaMalloc
  * (their device memory is owned by another allocator, such as a framework's

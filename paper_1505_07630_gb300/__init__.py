@@ -5,6 +5,7 @@ include/ldupcg.h); this package holds its build script, the ctypes binding
 and the autograd wrapper.  PyTorch supplies device memory and streams only.
 """
 from .ldupcg import (LduAmg, LduError, LduMatrix, amg_from_system, amg_pcg_solve,  # noqa: F401
+                     amg_pipecg_solve,
                      ldu_amg_aggregates, ldu_amg_create, ldu_amg_destroy, ldu_amg_info,
                      ldu_amg_vcycle)
 from .ldupcg import (from_system, from_systems, ldu_batch_info,  # noqa: F401

@@ -335,6 +335,7 @@ struct DCsr {
 // scalars of the outer PCG, resident on the device between kernels
 struct AmgScalars {
     double tol2, bn2, thr2, rr, rz, pq, alpha, beta;
+    double gamma, delta, gamma_old, alpha_old;   // pipelined CG
     int it, maxit;
     int done;      // 1: the remaining kernels of the iteration return at once
     int conv;      // 1: the recursive residual met the tolerance
@@ -771,6 +772,139 @@ __global__ void __launch_bounds__(kThreads) k_amg_xr(int n, const double *__rest
     }
 }
 
+// ---- pipelined PCG (Ghysels & Vanroose) with the FP64 cycle ------------------
+
+// w = A u with gamma = (r, u) and delta = (w, u); the cycle's next input
+// t0 = (w/d) w; the recurrences restart (beta = 0) at the next update
+__global__ void __launch_bounds__(kThreads) k_pp_init(DSell<double> A, const double *__restrict__ d,
+                                                      const double *__restrict__ u,
+                                                      const double *__restrict__ r,
+                                                      double *__restrict__ w,
+                                                      const double *__restrict__ wd,
+                                                      double *__restrict__ t, AmgScalars *S,
+                                                      double *part, unsigned *count) {
+    const int lane = threadIdx.x & 31;
+    double g = 0.0, dl = 0.0;
+    FOR_SLICES(A) {
+        const int row = s * 32 + lane;
+        const double off = sell_row(A, s, lane, [&](int c) { return u[c]; });
+        if (row < A.n) {
+            const double ui = u[row];
+            const double wi = fma(d[row], ui, off);
+            w[row] = wi;
+            if (wd)
+                t[row] = wd[row] * wi;
+            g = fma(r[row], ui, g);
+            dl = fma(wi, ui, dl);
+        }
+    }
+    double v[2] = {g, dl}, tot[2];
+    if (grid_sum_last<2>(v, part, count, tot) && threadIdx.x == 0) {
+        S->gamma = tot[0];
+        S->delta = tot[1];
+        S->restart = 1;
+        S->done = 0;
+        S->conv = 0;
+    }
+}
+
+// y = A x on the fine level (FP64)
+__global__ void __launch_bounds__(kThreads) k_pp_spmv(DSell<double> A, const double *__restrict__ d,
+                                                      const double *__restrict__ x,
+                                                      double *__restrict__ y,
+                                                      const AmgScalars *S) {
+    if (S->done)
+        return;
+    const int lane = threadIdx.x & 31;
+    FOR_SLICES(A) {
+        const int row = s * 32 + lane;
+        const double off = sell_row(A, s, lane, [&](int c) { return x[c]; });
+        if (row < A.n)
+            y[row] = fma(d[row], x[row], off);
+    }
+}
+
+struct PipeVecs {
+    const double *m, *nv;
+    double *z, *q, *s, *p, *x, *r, *u, *w;
+};
+
+// one pipelined step: beta and alpha from the last step's scalars (every
+// thread forms the same values), the eight recurrences, the cycle's next
+// input t0 = (w/d) w, and (r, u), (w, u), (r, r) for the next step; the
+// last block counts the step and tests convergence
+__global__ void __launch_bounds__(kThreads) k_pp_update(int n, PipeVecs V,
+                                                        const double *__restrict__ wd,
+                                                        double *__restrict__ t, AmgScalars *S,
+                                                        double *part, unsigned *count) {
+    if (S->done)
+        return;
+    const int restart = S->restart;
+    const double gamma = S->gamma, delta = S->delta;
+    double beta = 0.0, den = delta;
+    if (!restart) {
+        beta = gamma / S->gamma_old;
+        den = delta - beta * gamma / S->alpha_old;
+    }
+    const bool ok = den > 0.0 && gamma > 0.0;
+    const double alpha = ok ? gamma / den : 0.0;
+    double g = 0.0, dl = 0.0, rr = 0.0;
+    if (ok) {
+        for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+            double zi, qi, si, pi;
+            if (restart) {
+                zi = V.nv[i];
+                qi = V.m[i];
+                si = V.w[i];
+                pi = V.u[i];
+            } else {
+                zi = fma(beta, V.z[i], V.nv[i]);
+                qi = fma(beta, V.q[i], V.m[i]);
+                si = fma(beta, V.s[i], V.w[i]);
+                pi = fma(beta, V.p[i], V.u[i]);
+            }
+            V.z[i] = zi;
+            V.q[i] = qi;
+            V.s[i] = si;
+            V.p[i] = pi;
+            V.x[i] = fma(alpha, pi, V.x[i]);
+            const double ri = fma(-alpha, si, V.r[i]);
+            const double ui = fma(-alpha, qi, V.u[i]);
+            const double wi = fma(-alpha, zi, V.w[i]);
+            V.r[i] = ri;
+            V.u[i] = ui;
+            V.w[i] = wi;
+            if (wd)
+                t[i] = wd[i] * wi;
+            g = fma(ri, ui, g);
+            dl = fma(wi, ui, dl);
+            rr = fma(ri, ri, rr);
+        }
+    }
+    double v[3] = {g, dl, rr}, tot[3];
+    if (grid_sum_last<3>(v, part, count, tot) && threadIdx.x == 0) {
+        if (!ok) {
+            S->status = LDU_ERR_NOT_SPD;
+            S->done = 1;
+            return;
+        }
+        S->gamma_old = gamma;
+        S->alpha_old = alpha;
+        S->gamma = tot[0];
+        S->delta = tot[1];
+        S->rr = tot[2];
+        S->restart = 0;
+        S->it += 1;
+        if (tot[2] <= S->thr2) {
+            S->conv = 1;
+            S->done = 1;
+        } else if (S->it >= S->maxit) {
+            S->status = LDU_NOT_CONVERGED;
+            S->done = 1;
+        }
+    }
+}
+
 int grid_rows(int64_t n) {   // blocks for one thread per row (one warp per 32-row slice)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + kThreads - 1) / kThreads, kMaxBlocks));
 }
@@ -945,6 +1079,7 @@ struct ldu_amg {
     CoarseVals<float> c32;
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     float *r32 = nullptr, *z32 = nullptr;   // float cycle's input and output
+    double *pv[7] = {};             // pipelined CG: u, w, m, n, z, q, s (allocated on first use)
     double *part = nullptr;
     unsigned *count = nullptr;
     AmgScalars *S = nullptr;        // device
@@ -989,6 +1124,9 @@ void free_amg(ldu_amg *M) {
     for (void *p : ptrs)
         if (p)
             cudaFree(p);
+    for (double *v : M->pv)
+        if (v)
+            cudaFree(v);
     if (M->S_host)
         cudaFreeHost(M->S_host);
     delete M;
@@ -1150,6 +1288,120 @@ int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int 
     } else if (bn2 > 0.0) {
         k_amg_residual<T><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, nullptr, nullptr, nullptr, 1,
                                                    S, M->part, M->count);
+        if ((rc = read_scalars(M, st)) != LDU_OK)
+            return rc;
+        tr = std::sqrt(H->rr / bn2);
+    }
+    if (iters)
+        *iters = it;
+    if (relres)
+        *relres = tr;
+    return status;
+}
+
+// pipelined PCG with the FP64 cycle (Table 2's AMG-PipeCG): per step one
+// cycle m = V(w), one product n = A m and one update pass that also forms
+// the step's three dot products
+int pipe_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
+              double *relres, cudaStream_t st) {
+    const DSell<double> A = M->fine();
+    const double *d = M->fine_d();
+    const int64_t n = M->n;
+    const int ga = grid_rows(n);
+    for (double *&v : M->pv)
+        if (!v) {
+            cudaError_t e = alloc(&v, n, &M->device_bytes);
+            if (e != cudaSuccess)
+                return cuda_status(e);
+        }
+    double *u = M->pv[0], *w = M->pv[1], *m = M->pv[2], *nv = M->pv[3];
+    const PipeVecs V{m, nv, M->pv[4], M->pv[5], M->pv[6], M->p, x, M->r, u, w};
+    const double *wd0 = M->lev.empty() ? nullptr : M->lev[0].v64.wd;
+    double *t0 = M->lev.empty() ? nullptr : M->lev[0].v64.t;
+    AmgScalars *S = M->S, *H = M->S_host;
+    std::memset(H, 0, sizeof(AmgScalars));
+    H->tol2 = tol * tol;
+    H->maxit = maxit;
+    H->status = LDU_OK;
+    cudaError_t e = cudaMemcpyAsync(S, H, sizeof(AmgScalars), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    int rc = LDU_OK;
+    // r = b - A x0 (and the cycle's input), u = V(r), w = A u, gamma, delta
+    auto start = [&](int mode) {
+        k_amg_residual<double><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, wd0, t0, nullptr, mode,
+                                                        S, M->part, M->count);
+        int r2 = vcycle<double>(M, 0, M->r, u, false, nullptr, st);
+        if (r2 != LDU_OK)
+            return r2;
+        k_pp_init<<<ga, kThreads, 0, st>>>(A, d, u, M->r, w, wd0, t0, S, M->part, M->count);
+        return cuda_status(cudaGetLastError());
+    };
+    if ((rc = start(0)) != LDU_OK)
+        return rc;
+    if ((rc = read_scalars(M, st)) != LDU_OK)
+        return rc;
+    int status = LDU_NOT_CONVERGED, it = 0;
+    bool confirmed = false;
+    const double bn2 = H->bn2, thr2 = H->thr2;
+    if (bn2 == 0.0) {
+        cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st);
+        status = LDU_OK;
+    } else if (H->rr <= thr2) {
+        status = LDU_OK;
+        confirmed = true;
+    } else if (maxit > 0) {
+        double rr_prev = H->rr;
+        int it_prev = 0, batch = 4;
+        for (;;) {
+            for (int g = 0; g < batch; ++g) {
+                if ((rc = vcycle<double>(M, 0, w, m, false, &S->done, st)) != LDU_OK)
+                    return rc;
+                k_pp_spmv<<<ga, kThreads, 0, st>>>(A, d, m, nv, S);
+                k_pp_update<<<ga, kThreads, 0, st>>>((int)n, V, wd0, t0, S, M->part, M->count);
+            }
+            if ((rc = read_scalars(M, st)) != LDU_OK)
+                return rc;
+            it = H->it;
+            if (H->status == LDU_ERR_NOT_SPD) {
+                status = LDU_ERR_NOT_SPD;
+                break;
+            }
+            if (H->conv) {
+                k_amg_residual<double><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, nullptr,
+                                                                nullptr, nullptr, 1, S, M->part,
+                                                                M->count);
+                if ((rc = read_scalars(M, st)) != LDU_OK)
+                    return rc;
+                if (H->rr <= thr2) {
+                    status = LDU_OK;
+                    confirmed = true;
+                    break;
+                }
+                if (it >= maxit)
+                    break;
+                // restart the recurrences from the true residual
+                if ((rc = start(1)) != LDU_OK)
+                    return rc;
+                continue;
+            }
+            if (H->status == LDU_NOT_CONVERGED)
+                break;
+            const double rho = std::pow(H->rr / rr_prev, 1.0 / std::max(1, it - it_prev));
+            double left = 8.0;
+            if (rho > 0.0 && rho < 1.0)
+                left = std::min(8.0, std::log(thr2 / H->rr) / std::log(rho));
+            batch = std::min(maxit - it, std::max(1, (int)std::lround(left)));
+            rr_prev = H->rr;
+            it_prev = it;
+        }
+    }
+    double tr = 0.0;
+    if (bn2 > 0.0 && confirmed) {
+        tr = std::sqrt(H->rr / bn2);
+    } else if (bn2 > 0.0) {
+        k_amg_residual<double><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, nullptr, nullptr,
+                                                        nullptr, 1, S, M->part, M->count);
         if ((rc = read_scalars(M, st)) != LDU_OK)
             return rc;
         tr = std::sqrt(H->rr / bn2);
@@ -1348,7 +1600,7 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
     CKA(alloc(&M->q, n, nb));
     CKA(alloc(&M->r32, n, nb));
     CKA(alloc(&M->z32, n, nb));
-    CKA(alloc(&M->part, 2 * kMaxBlocks, nb));
+    CKA(alloc(&M->part, 3 * kMaxBlocks, nb));
     CKA(alloc(&M->count, 1, nb));
     CKA(cudaMemset(M->count, 0, sizeof(unsigned)));
     CKA(alloc(&M->S, 1, nb));
@@ -1412,6 +1664,13 @@ int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit,
     if (precision == LDU_FP64)
         return pcg_loop<double>(M, b, x, tol, maxit, iters, relres, (cudaStream_t)stream);
     return pcg_loop<float>(M, b, x, tol, maxit, iters, relres, (cudaStream_t)stream);
+}
+
+int amg_pipecg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
+                     double *relres, ldu_stream_t stream) {
+    if (!M || !b || !x || b == x || maxit < 0 || !(tol >= 0.0))
+        return LDU_ERR_BAD_ARG;
+    return pipe_loop(M, b, x, tol, maxit, iters, relres, (cudaStream_t)stream);
 }
 
 }  // extern "C"

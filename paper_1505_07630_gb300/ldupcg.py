@@ -141,6 +141,8 @@ def lib():
         L.ldu_amg_vcycle.restype = i
         L.amg_pcg_solve.argtypes = [_vp, _vp, _vp, d, i, i, pi, pd, _vp]
         L.amg_pcg_solve.restype = i
+        L.amg_pipecg_solve.argtypes = [_vp, _vp, _vp, d, i, pi, pd, _vp]
+        L.amg_pipecg_solve.restype = i
         L.ldu_status_string.argtypes = [i]
         L.ldu_status_string.restype = ctypes.c_char_p
         for name in ("ldu_create", "ldu_update_values", "ldu_set_face_coeffs", "ldu_spmv",
@@ -511,6 +513,20 @@ def amg_pcg_solve(M, b, x=None, tol=1e-8, maxit=500, precision="fp64", stream=No
                              ctypes.byref(it), ctypes.byref(rr), _stream(stream))
     if check:
         _check(st, "amg_pcg_solve")
+    return x, it.value, rr.value, st
+
+
+def amg_pipecg_solve(M, b, x=None, tol=1e-8, maxit=500, stream=None, check=True):
+    """Pipelined AMG-preconditioned CG (FP64 cycle); returns (x, iters, relres, status)."""
+    if x is None:
+        x = torch.zeros_like(b)
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    st = lib().amg_pipecg_solve(M.handle, _dev(b, torch.float64, M.n, "b"),
+                                _dev(x, torch.float64, M.n, "x"), float(tol), int(maxit),
+                                ctypes.byref(it), ctypes.byref(rr), _stream(stream))
+    if check:
+        _check(st, "amg_pipecg_solve")
     return x, it.value, rr.value, st
 
 

@@ -230,3 +230,58 @@ def test_full_size_128_converges(pkg):
         assert st == 0 and relres <= 1e-8
         assert it <= 60   # Table 2 reports 32 for the paper's aggregation AMG at 128^3
     M.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_pipelined_amg_pcg_matches_oracle(pkg, amg, name):
+    s = CASES[name]()
+    M = pkg.amg_from_system(s)
+    r = amg.amg_pipecg(s, tol=1e-8, maxit=200)
+    x, it, relres, st = pkg.amg_pipecg_solve(M, dev(s.b), tol=1e-8, maxit=200)
+    assert st == 0 and relres <= 1e-8
+    assert abs(it - r.iters) <= 1, (it, r.iters)
+    A = amg.csr_of(s)
+    assert np.linalg.norm(s.b - A @ x.cpu().numpy()) <= 1.0001e-8 * np.linalg.norm(s.b)
+    M.close()
+
+
+def test_pipelined_iterates_equal_pcg_iterates(pkg):
+    """After k steps the pipelined and the plain AMG-PCG hold the same
+    iterate up to rounding (both on the device, FP64 cycle)."""
+    s = CASES["lognormal_20x17x13"]()
+    M = pkg.amg_from_system(s)
+    for k in (1, 4, 9):
+        x1, it1, _, st1 = pkg.amg_pcg_solve(M, dev(s.b), tol=1e-30, maxit=k, check=False)
+        x2, it2, _, st2 = pkg.amg_pipecg_solve(M, dev(s.b), tol=1e-30, maxit=k, check=False)
+        assert st1 == st2 == 1 and it1 == it2 == k
+        a, b = x1.cpu().numpy(), x2.cpu().numpy()
+        assert np.max(np.abs(a - b)) <= 1e-9 * np.max(np.abs(a)), k
+    M.close()
+
+
+def test_pipelined_edge_cases(pkg, amg):
+    s = lc.poisson_box(7, 6, 5, diffusivity="lognormal", seed=2)   # its own coarsest level
+    M = pkg.amg_from_system(s)
+    x, it, relres, st = pkg.amg_pipecg_solve(M, dev(s.b), tol=1e-10)
+    assert st == 0 and it == 1 and relres <= 1e-10
+    x, it, relres, st = pkg.amg_pipecg_solve(M, torch.zeros(s.n, dtype=torch.float64,
+                                                            device="cuda"))
+    assert st == 0 and it == 0 and float(x.abs().max()) == 0.0
+    M.close()
+    s = lc.poisson_box(12)
+    M = pkg.amg_from_system(s)
+    x0 = np.random.default_rng(5).uniform(-1, 1, s.n)
+    x, it, relres, st = pkg.amg_pipecg_solve(M, dev(s.b), x=dev(x0), tol=1e-9)
+    assert st == 0 and relres <= 1e-9
+    A = amg.csr_of(s)
+    assert np.linalg.norm(s.b - A @ x.cpu().numpy()) <= 1.0001e-9 * np.linalg.norm(s.b)
+    M.close()
+
+
+def test_pipelined_full_size_128(pkg):
+    s = configs.config2(128)
+    M = pkg.amg_from_system(s)
+    _, it1, rr1, st1 = pkg.amg_pcg_solve(M, dev(s.b), tol=1e-8, precision="fp64")
+    _, it2, rr2, st2 = pkg.amg_pipecg_solve(M, dev(s.b), tol=1e-8)
+    assert st1 == st2 == 0 and rr2 <= 1e-8 and abs(it1 - it2) <= 1
+    M.close()
