@@ -5,7 +5,7 @@ benchmark's CPU-baseline leg, never by the library.  It shares no code with
 the CUDA path; the two meet only in the seeded inputs of `ldu_cases`.
 
 Routines (C source in ldu_oracle.c, each citing what it restates):
-  spmv, pcg, pipecg, mixed_pipecg, face_grad, harmonic_coeffs, harmonic_grad,
+  spmv, pcg, pipecg, mixed_pipecg, face_grad, value_grad, harmonic_coeffs, harmonic_grad,
   lu_solve, true_relres
 plus two plain numpy helpers, `dense` (the LDU matrix written out densely)
 and `matrix_from_coef` (the FVM matrix of a set of face coefficients).
@@ -44,6 +44,8 @@ def lib():
         L.or_mixed_pipecg.restype = c_int
         L.or_face_grad.argtypes = [i64, _i32, _i32, _d, _d, _d]
         L.or_face_grad.restype = None
+        L.or_value_grad.argtypes = [i64, i64, _i32, _i32, _d, _d, _d, _d, _d]
+        L.or_value_grad.restype = None
         L.or_harmonic_coeffs.argtypes = [i64, i64, _i32, _i32, _d, _d, _d, _d, _d]
         L.or_harmonic_coeffs.restype = None
         L.or_harmonic_grad.argtypes = [i64, i64, _i32, _i32, _d, _d, _d, _d, _d, _d]
@@ -151,6 +153,20 @@ def face_grad(owner, neighbour, lam, x):
     lib().or_face_grad(ctypes.c_int64(ow.shape[0]), _p(ow, _i32), _p(nb, _i32), _p(lam), _p(x),
                        _p(g))
     return g
+
+
+def value_grad(owner, neighbour, lam, x):
+    """(ddiag, dupper, dlower): dL/dA_ij = -lambda_i x_j for every stored LDU value."""
+    ow = np.ascontiguousarray(owner, dtype=np.int32)
+    nb = np.ascontiguousarray(neighbour, dtype=np.int32)
+    lam = _f64(lam)
+    x = _f64(x)
+    dd = np.empty(x.shape[0])
+    du = np.empty(ow.shape[0])
+    dl = np.empty(ow.shape[0])
+    lib().or_value_grad(ctypes.c_int64(x.shape[0]), ctypes.c_int64(ow.shape[0]), _p(ow, _i32),
+                        _p(nb, _i32), _p(lam), _p(x), _p(dd), _p(du), _p(dl))
+    return dd, du, dl
 
 
 def harmonic_coeffs(owner, neighbour, k, g, bfac):

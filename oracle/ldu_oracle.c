@@ -16,6 +16,7 @@
  *   or_mixed_pipecg   FP32 pipelined PCG with FP64 residual replacement and FP64
  *                     solution accumulation (reliable updates or defect correction)
  *   or_face_grad      adjoint face-coefficient gradient -(l_o - l_n)(x_o - x_n)
+ *   or_value_grad     adjoint gradient of every stored LDU value: dL/dA_ij = -l_i x_j
  *   or_harmonic_coeffs / or_harmonic_grad
  *                     face coefficients from cell diffusivities through the
  *                     harmonic mean, and the chain rule back to the cells
@@ -580,6 +581,22 @@ void or_face_grad(int64_t nf, const int32_t *own, const int32_t *nbr,
 {
     for (int64_t f = 0; f < nf; f++)
         grad[f] = -(lambda[own[f]] - lambda[nbr[f]]) * (x[own[f]] - x[nbr[f]]);
+}
+
+/* Gradient of L(x(A)) with respect to each stored entry of an LDU matrix
+ * taken as independent (upper and lower need not stay equal): differentiating
+ * A x = b gives dx = -A^-1 dA x, so dL/dA_ij = -lambda_i x_j with
+ * lambda = A^-T dL/dx.  upper[f] = A[o, n], lower[f] = A[n, o], diag = A[i, i]. */
+void or_value_grad(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
+                   const double *lambda, const double *x, double *ddiag, double *dup,
+                   double *dlo)
+{
+    for (int64_t i = 0; i < n; i++)
+        ddiag[i] = -lambda[i] * x[i];
+    for (int64_t f = 0; f < nf; f++) {
+        dup[f] = -lambda[own[f]] * x[nbr[f]];
+        dlo[f] = -lambda[nbr[f]] * x[own[f]];
+    }
 }
 
 /* ---- cell diffusivity -> face coefficients (harmonic mean) -----------------

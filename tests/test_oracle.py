@@ -355,3 +355,43 @@ def test_table2_plain_cg_magnitude(oracle_mod):
     # the paper's 128/64 ratio is 636/325 = 1.96
     ratio = its[64] / its[32]
     assert 1.6 <= ratio <= 2.4
+
+
+def test_value_gradient_matches_nonsymmetric_finite_differences(oracle_mod):
+    """dL/dA_ij = -lambda_i x_j for upper, lower and diagonal entries taken
+    one at a time, so every perturbation but the diagonal's makes A
+    non-symmetric: central differences through the oracle's dense LU of the
+    perturbed matrix (lambda from A^T).  The sum over a face's four entries
+    reproduces the face-coefficient gradient."""
+    s = lc.poisson_box(3, 3, 4, diffusivity="lognormal", seed=9)
+    g = np.random.default_rng(1)
+    x_t = g.uniform(-1, 1, s.n)
+    base = oracle_mod.dense(s)
+
+    def loss(A):
+        x = oracle_mod.lu_solve(A, s.b)
+        return x
+
+    x = loss(base)
+    lam = oracle_mod.lu_solve(base.T, x - x_t)
+    dd, du, dl = oracle_mod.value_grad(s.owner, s.neighbour, lam, x)
+    h = 1e-6
+
+    def fd(i, j):
+        Ap = base.copy()
+        Am = base.copy()
+        Ap[i, j] += h
+        Am[i, j] -= h
+        xp, xm = loss(Ap), loss(Am)
+        return 0.5 * np.sum((xp - xm) * (xp + xm - 2 * x_t)) / (2 * h)
+
+    scale = max(np.max(np.abs(du)), np.max(np.abs(dl)), np.max(np.abs(dd)))
+    for f in range(0, s.nfaces, 3):
+        o, n = int(s.owner[f]), int(s.neighbour[f])
+        assert abs(fd(o, n) - du[f]) <= 1e-5 * scale
+        assert abs(fd(n, o) - dl[f]) <= 1e-5 * scale
+    for i in range(0, s.n, 4):
+        assert abs(fd(i, i) - dd[i]) <= 1e-5 * scale
+    # c_f enters as upper = lower = -c_f and +c_f on both diagonals
+    gc = oracle_mod.face_grad(s.owner, s.neighbour, lam, x)
+    assert np.allclose(-du - dl + dd[s.owner] + dd[s.neighbour], gc, rtol=1e-12, atol=1e-15)
