@@ -245,6 +245,18 @@ int ldu_face_grad(const ldu_matrix *A, const double *lambda, const double *x, do
 int ldu_diag_grad(const ldu_matrix *A, const double *lambda, const double *x, double *ddiag,
                   ldu_stream_t stream);
 
+/* Gradient of a loss with respect to every stored off-diagonal value taken
+ * independently (upper and lower need not stay equal: the derivative of the
+ * solution map in non-symmetric directions, exact at the symmetric A that
+ * the solvers accept): differentiating A x = b gives dL/dA_ij = -lambda_i x_j
+ * with lambda = A^-T dL/dx (= A^-1 dL/dx here), so
+ *   dupper[f] = -lambda[owner[f]] x[neighbour[f]]
+ *   dlower[f] = -lambda[neighbour[f]] x[owner[f]]
+ * (device double[nFaces], the caller's face order); the diagonal's gradient
+ * -lambda_i x_i is ldu_diag_grad's.  Queued on stream. */
+int ldu_value_grad(const ldu_matrix *A, const double *lambda, const double *x, double *dupper,
+                   double *dlower, ldu_stream_t stream);
+
 /* Face coefficients and wall terms of the FVM Laplacian from cell
  * diffusivities (Eq. 8's laplacian operator, discretised as in Sec. 5's
  * lduMatrix): with the harmonic mean k_f = 2 k_o k_n / (k_o + k_n) of the

@@ -11,9 +11,10 @@ from .ldupcg import (LduAmg, LduError, LduMatrix, amg_from_system, amg_pcg_solve
 from .ldupcg import (from_system, from_systems, ldu_batch_info,  # noqa: F401
                      ldu_batch_results, ldu_batch_schedule, ldu_create, ldu_create_batched,
                      ldu_destroy, ldu_diag_grad, ldu_harmonic_coeffs, ldu_harmonic_grad,
-                     ldu_heat_steps, ldu_piso_pressure,
+                     ldu_heat_steps, ldu_piso_pressure, ldu_value_grad,
                      pcg_solve_batched, pcg_solve_batched_async,
                      ldu_face_grad, ldu_set_face_coeffs, ldu_spmv, ldu_update_values, lib,
                      library_path, pcg_solve, pcg_solve_ldu_noalloc, pipecg_solve,
                      status_string)
-from .autograd import HarmonicCoeffs, LduSolve, harmonic_coeffs, ldu_solve  # noqa: F401,E402
+from .autograd import (HarmonicCoeffs, LduSolve, LduSolveValues, harmonic_coeffs,  # noqa: F401,E402
+                       ldu_solve, ldu_solve_values)

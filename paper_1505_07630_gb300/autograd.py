@@ -11,6 +11,12 @@ solve, and
 The handle may be a batched handle: b, x, c and diag_extra are then the
 systems' arrays concatenated, and both solves are one batched launch.
 
+ldu_solve_values is the same solve differentiable in the stored LDU values
+themselves (diag, upper, lower; the forward values must be symmetric, as CG
+needs), with dL/dA_ij = -lambda_i x_j: dL/ddiag_i = -lambda_i x_i
+(ldu_diag_grad), dL/dupper_f = -lambda_o x_n, dL/dlower_f = -lambda_n x_o
+(ldu_value_grad) -- the derivative also in non-symmetric directions.
+
 harmonic_coeffs maps cell diffusivities k to (c, diag_extra) through the
 harmonic-mean faces of the FVM Laplacian (ldu_harmonic_coeffs), with
     dL/dk_P = dL/d(diag_extra)_P bfac_P
@@ -73,6 +79,48 @@ def ldu_solve(A, coef, diag_extra, b, precision="fp64", tol=1e-12, maxit=100000,
     precision: 'fp64' (Jacobi-PCG), 'pipe' (FP64 pipelined) or 'mixed'."""
     cfg = dict(precision=precision, tol=tol, maxit=maxit, x0=x0, check=check, kw=kw)
     return LduSolve.apply(coef, diag_extra, b, A, cfg)
+
+
+class LduSolveValues(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, diag, upper, lower, b, A, cfg):
+        diag = diag.detach().contiguous()
+        upper = upper.detach().contiguous()
+        lower = lower.detach().contiguous()
+        if not torch.equal(upper, lower):
+            raise ValueError("ldu_solve_values: CG needs symmetric values (upper == lower)")
+        ldupcg.ldu_update_values(A, diag, upper, lower)
+        x = torch.zeros_like(b)
+        if cfg.get("x0") is not None:
+            x.copy_(cfg["x0"])
+        _solve(A, b.detach().contiguous(), x, cfg)
+        ctx.save_for_backward(diag, upper, lower, x)
+        ctx.A = A
+        ctx.cfg = cfg
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        diag, upper, lower, x = ctx.saved_tensors
+        A = ctx.A
+        ldupcg.ldu_update_values(A, diag, upper, lower)
+        lam = torch.zeros_like(x)
+        _solve(A, gx.detach().contiguous(), lam, ctx.cfg)   # A^T = A
+        g_diag = ldupcg.ldu_diag_grad(A, lam, x) if ctx.needs_input_grad[0] else None
+        g_up = g_lo = None
+        if ctx.needs_input_grad[1] or ctx.needs_input_grad[2]:
+            g_up, g_lo = ldupcg.ldu_value_grad(A, lam, x)
+        g_b = lam if ctx.needs_input_grad[3] else None
+        return (g_diag, g_up if ctx.needs_input_grad[1] else None,
+                g_lo if ctx.needs_input_grad[2] else None, g_b, None, None)
+
+
+def ldu_solve_values(A, diag, upper, lower, b, precision="fp64", tol=1e-12, maxit=100000,
+                     x0=None, check=True, **kw):
+    """x = A^-1 b for the LDU values (diag, upper, lower), differentiable in
+    all three and in b.  precision as ldu_solve."""
+    cfg = dict(precision=precision, tol=tol, maxit=maxit, x0=x0, check=check, kw=kw)
+    return LduSolveValues.apply(diag, upper, lower, b, A, cfg)
 
 
 class HarmonicCoeffs(torch.autograd.Function):

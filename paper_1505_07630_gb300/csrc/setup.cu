@@ -436,6 +436,17 @@ int ldu_face_grad(const ldu_matrix *A, const double *lambda, const double *x, do
     return cuda_status(cudaGetLastError());
 }
 
+int ldu_value_grad(const ldu_matrix *A, const double *lambda, const double *x, double *dupper,
+                   double *dlower, ldu_stream_t stream) {
+    if (!A || (A->nf > 0 && (!lambda || !x || !dupper || !dlower)))
+        return LDU_ERR_BAD_ARG;
+    if (A->nf == 0)
+        return LDU_OK;
+    k_value_grad<<<blocks_for(A->nf, 256), 256, 0, (cudaStream_t)stream>>>(
+        A->nf, A->owner, A->neighbour, lambda, x, dupper, dlower);
+    return cuda_status(cudaGetLastError());
+}
+
 int ldu_harmonic_coeffs(const ldu_matrix *A, const double *k, const double *g,
                         const double *bfac, double *coef, double *diag_extra,
                         ldu_stream_t stream) {

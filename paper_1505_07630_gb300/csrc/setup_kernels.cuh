@@ -308,4 +308,17 @@ __global__ void k_face_grad(int64_t nf, const int32_t *__restrict__ own,
     }
 }
 
+// dL/dupper_f = -lambda_o x_n, dL/dlower_f = -lambda_n x_o (dL/dA_ij = -lambda_i x_j)
+__global__ void k_value_grad(int64_t nf, const int32_t *__restrict__ own,
+                             const int32_t *__restrict__ nbr, const double *__restrict__ lam,
+                             const double *__restrict__ x, double *__restrict__ gup,
+                             double *__restrict__ glo) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int o = own[f], nb = nbr[f];
+        gup[f] = -lam[o] * x[nb];
+        glo[f] = -lam[nb] * x[o];
+    }
+}
+
 }  // namespace

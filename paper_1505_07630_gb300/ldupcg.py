@@ -97,6 +97,8 @@ def lib():
         L.ldu_face_grad.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.ldu_diag_grad.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.ldu_diag_grad.restype = i
+        L.ldu_value_grad.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
+        L.ldu_value_grad.restype = i
         L.ldu_heat_steps.argtypes = [_vp, _vp, _vp, i, d, i, i, ctypes.POINTER(PcgOpts), pi, pd,
                                      _vp]
         L.ldu_heat_steps.restype = i
@@ -328,6 +330,20 @@ def ldu_diag_grad(A, lam, x, out=None, stream=None):
                              _dev(out, torch.float64, A.n, "ddiag"), _stream(stream))
     _check(st, "ldu_diag_grad", allow_not_converged=False)
     return out
+
+
+def ldu_value_grad(A, lam, x, dupper=None, dlower=None, stream=None):
+    """(dL/dupper, dL/dlower) = (-lambda_o x_n, -lambda_n x_o) per face."""
+    if dupper is None:
+        dupper = torch.empty(A.nfaces, dtype=torch.float64, device=x.device)
+    if dlower is None:
+        dlower = torch.empty(A.nfaces, dtype=torch.float64, device=x.device)
+    st = lib().ldu_value_grad(A.handle, _dev(lam, torch.float64, A.n, "lam"),
+                              _dev(x, torch.float64, A.n, "x"),
+                              _dev(dupper, torch.float64, A.nfaces, "dupper"),
+                              _dev(dlower, torch.float64, A.nfaces, "dlower"), _stream(stream))
+    _check(st, "ldu_value_grad", allow_not_converged=False)
+    return dupper, dlower
 
 
 def ldu_heat_steps(A, mass, T, nsteps, tol=1e-8, maxit=20000, precision="mixed", stream=None,

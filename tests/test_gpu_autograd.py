@@ -232,3 +232,54 @@ def test_cell_diffusivity_gradient_finite_differences(pkg):
         fd = float(0.5 * ((xp - xm) * (xp + xm - 2 * xt)).sum()) / (2 * h)
         assert abs(fd - gk[i]) <= 1e-5 * max(abs(gk[i]), np.abs(gk).max()), (i, fd, gk[i])
     A.close()
+
+
+def test_value_grad_kernel_is_bit_exact(pkg, oracle_mod):
+    s = lc.poisson_box(9, 7, 5, diffusivity="lognormal", seed=12)
+    A = pkg.from_system(s)
+    rng = np.random.default_rng(4)
+    lam, x = rng.standard_normal(s.n), rng.standard_normal(s.n)
+    gu, gl = pkg.ldu_value_grad(A, dev(lam), dev(x))
+    _, ou, ol = oracle_mod.value_grad(s.owner, s.neighbour, lam, x)
+    assert np.array_equal(gu.cpu().numpy(), ou) and np.array_equal(gl.cpu().numpy(), ol)
+    A.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_value_gradients_match_oracle_adjoint(pkg, oracle_mod, precision):
+    """ldu_solve_values: gradients with respect to diag, upper, lower (each
+    entry independent, so including non-symmetric directions) and b, against
+    the oracle's dense adjoint; the oracle's value gradient is itself pinned
+    by non-symmetric finite differences."""
+    s = lc.poisson_box(6, 5, 4, diffusivity="lognormal", seed=3)
+    A = pkg.from_system(s)
+    xt = np.random.default_rng(0).uniform(-1, 1, s.n)
+    diag = dev(s.diag).requires_grad_(True)
+    up = dev(s.upper).requires_grad_(True)
+    lo = dev(s.lower).requires_grad_(True)
+    b = dev(s.b).requires_grad_(True)
+    x = pkg.ldu_solve_values(A, diag, up, lo, b, precision=precision, tol=1e-13)
+    (0.5 * ((x - dev(xt)) ** 2).sum()).backward()
+    M = oracle_mod.dense(s)
+    x_o = oracle_mod.lu_solve(M, s.b)
+    lam = oracle_mod.lu_solve(M.T, x_o - xt)
+    gd, gu, gl = oracle_mod.value_grad(s.owner, s.neighbour, lam, x_o)
+    for got, ref in ((diag.grad, gd), (up.grad, gu), (lo.grad, gl), (b.grad, lam)):
+        got = got.cpu().numpy()
+        assert np.linalg.norm(got - ref) <= 1e-8 * np.linalg.norm(ref), precision
+    # the face-coefficient chain: c_f enters as upper = lower = -c_f and +c_f on both diagonals
+    gc = oracle_mod.face_grad(s.owner, s.neighbour, lam, x_o)
+    g = (-up.grad - lo.grad + diag.grad[torch.as_tensor(s.owner, device="cuda").long()]
+         + diag.grad[torch.as_tensor(s.neighbour, device="cuda").long()]).cpu().numpy()
+    assert np.linalg.norm(g - gc) <= 1e-8 * np.linalg.norm(gc)
+    A.close()
+
+
+def test_value_solve_refuses_nonsymmetric_values(pkg):
+    s = lc.poisson_box(4, 4, 4, diffusivity="lognormal", seed=5)
+    A = pkg.from_system(s)
+    lo = dev(s.lower)
+    lo[3] *= 1.01
+    with pytest.raises(ValueError):
+        pkg.ldu_solve_values(A, dev(s.diag), dev(s.upper), lo, dev(s.b))
+    A.close()
