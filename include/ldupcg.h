@@ -452,7 +452,10 @@ int ldu_amg_vcycle(ldu_amg *M, int precision, const void *b, void *x, ldu_stream
  *              the stopping test is on the double residual either way.
  * NOT_SPD on a breakdown (p^T A p <= 0), NOT_CONVERGED when maxit is
  * reached.  Synchronises stream: the host reads the device-resident scalars
- * between batches of iterations sized from the observed convergence rate. */
+ * between batches of iterations sized from the observed convergence rate.
+ * One outer iteration (its 16 kernels) is captured as a CUDA graph on the
+ * hierarchy's private stream at the first call with a given x and replayed
+ * on `stream` for every iteration; a call with another x updates the graph. */
 int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int precision,
                   int *iters, double *relres, ldu_stream_t stream);
 

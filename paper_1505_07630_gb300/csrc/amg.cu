@@ -1080,6 +1080,11 @@ struct ldu_amg {
     double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     float *r32 = nullptr, *z32 = nullptr;   // float cycle's input and output
     double *pv[7] = {};             // pipelined CG: u, w, m, n, z, q, s (allocated on first use)
+    // one outer iteration captured as a CUDA graph per loop kind (CG with the
+    // float cycle, CG with the FP64 cycle, pipelined), keyed by the caller's x
+    cudaStream_t cap = nullptr;     // private stream the iterations are captured on
+    cudaGraphExec_t body[3] = {};
+    const void *body_x[3] = {};
     double *part = nullptr;
     unsigned *count = nullptr;
     AmgScalars *S = nullptr;        // device
@@ -1127,6 +1132,11 @@ void free_amg(ldu_amg *M) {
     for (double *v : M->pv)
         if (v)
             cudaFree(v);
+    for (cudaGraphExec_t g : M->body)
+        if (g)
+            cudaGraphExecDestroy(g);
+    if (M->cap)
+        cudaStreamDestroy(M->cap);
     if (M->S_host)
         cudaFreeHost(M->S_host);
     delete M;
@@ -1183,6 +1193,52 @@ int vcycle(ldu_amg *M, size_t l, const T *b, T *x, bool dot, const int *skip, cu
     return cuda_status(cudaGetLastError());
 }
 
+// The graph of one outer iteration of loop `kind` for the caller's x: the
+// cached one when x is the same, else the launches `body` makes on the
+// private stream are captured and replace the cached graph's parameters (or
+// a new graph is instantiated).  Every kernel of an iteration returns at once
+// when the scalars say the loop has stopped, so the graph can be launched
+// for a whole batch of iterations.
+template <typename F>
+int iteration_graph(ldu_amg *M, int kind, const void *x, F body, cudaGraphExec_t *out) {
+    if (M->body[kind] && M->body_x[kind] == x) {
+        *out = M->body[kind];
+        return LDU_OK;
+    }
+    cudaError_t e = cudaStreamBeginCapture(M->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    const int rc = body(M->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(M->cap, &graph);
+    if (rc != LDU_OK || e != cudaSuccess) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return rc != LDU_OK ? rc : cuda_status(e);
+    }
+    bool updated = false;
+    if (M->body[kind]) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(M->body[kind], graph, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();   // clear the update's error state
+            cudaGraphExecDestroy(M->body[kind]);
+            M->body[kind] = nullptr;
+        }
+    }
+    if (!updated)
+        e = cudaGraphInstantiate(&M->body[kind], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        M->body[kind] = nullptr;
+        M->body_x[kind] = nullptr;
+        return cuda_status(e);
+    }
+    M->body_x[kind] = x;
+    *out = M->body[kind];
+    return LDU_OK;
+}
+
 // the outer scalars to the pinned host copy (synchronises st)
 int read_scalars(ldu_amg *M, cudaStream_t st) {
     cudaError_t e = cudaMemcpyAsync(M->S_host, M->S, sizeof(AmgScalars), cudaMemcpyDeviceToHost, st);
@@ -1234,16 +1290,23 @@ int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int 
     } else if (maxit > 0) {
         // iterations in batches between host reads, sized from the observed
         // convergence rate so that few kernels run past the stopping point
+        cudaGraphExec_t step = nullptr;
+        rc = iteration_graph(M, f32 ? 0 : 1, x, [&](cudaStream_t cs) {
+            k_amg_p<T><<<ga, kThreads, 0, cs>>>((int)n, (const T *)cyc_z, M->p, S);
+            k_amg_q<<<ga, kThreads, 0, cs>>>(A, d, M->p, M->q, S, M->part, M->count);
+            k_amg_xr<T><<<ga, kThreads, 0, cs>>>((int)n, M->p, M->q, x, M->r, wd0, t0, bv, S,
+                                                 M->part, M->count);
+            return vcycle<T>(M, 0, cyc_b, cyc_z, true, &S->done, cs);
+        }, &step);
+        if (rc != LDU_OK)
+            return rc;
         double rr_prev = H->rr;
         int it_prev = 0, batch = 4;
         for (;;) {
             for (int g = 0; g < batch; ++g) {
-                k_amg_p<T><<<ga, kThreads, 0, st>>>((int)n, (const T *)cyc_z, M->p, S);
-                k_amg_q<<<ga, kThreads, 0, st>>>(A, d, M->p, M->q, S, M->part, M->count);
-                k_amg_xr<T><<<ga, kThreads, 0, st>>>((int)n, M->p, M->q, x, M->r, wd0, t0, bv, S,
-                                                     M->part, M->count);
-                if ((rc = vcycle<T>(M, 0, cyc_b, cyc_z, true, &S->done, st)) != LDU_OK)
-                    return rc;
+                const cudaError_t eg = cudaGraphLaunch(step, st);
+                if (eg != cudaSuccess)
+                    return cuda_status(eg);
             }
             if ((rc = read_scalars(M, st)) != LDU_OK)
                 return rc;
@@ -1351,14 +1414,24 @@ int pipe_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int
         status = LDU_OK;
         confirmed = true;
     } else if (maxit > 0) {
+        cudaGraphExec_t step = nullptr;
+        rc = iteration_graph(M, 2, x, [&](cudaStream_t cs) {
+            const int r2 = vcycle<double>(M, 0, w, m, false, &S->done, cs);
+            if (r2 != LDU_OK)
+                return r2;
+            k_pp_spmv<<<ga, kThreads, 0, cs>>>(A, d, m, nv, S);
+            k_pp_update<<<ga, kThreads, 0, cs>>>((int)n, V, wd0, t0, S, M->part, M->count);
+            return cuda_status(cudaGetLastError());
+        }, &step);
+        if (rc != LDU_OK)
+            return rc;
         double rr_prev = H->rr;
         int it_prev = 0, batch = 4;
         for (;;) {
             for (int g = 0; g < batch; ++g) {
-                if ((rc = vcycle<double>(M, 0, w, m, false, &S->done, st)) != LDU_OK)
-                    return rc;
-                k_pp_spmv<<<ga, kThreads, 0, st>>>(A, d, m, nv, S);
-                k_pp_update<<<ga, kThreads, 0, st>>>((int)n, V, wd0, t0, S, M->part, M->count);
+                const cudaError_t eg = cudaGraphLaunch(step, st);
+                if (eg != cudaSuccess)
+                    return cuda_status(eg);
             }
             if ((rc = read_scalars(M, st)) != LDU_OK)
                 return rc;
@@ -1605,6 +1678,7 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
     CKA(cudaMemset(M->count, 0, sizeof(unsigned)));
     CKA(alloc(&M->S, 1, nb));
     CKA(cudaMallocHost((void **)&M->S_host, sizeof(AmgScalars)));
+    CKA(cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
 #undef CKA
     *out = M;
     return LDU_OK;
