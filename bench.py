@@ -47,16 +47,16 @@ PROFILE = os.path.join(ROOT, "profiles", "k_mixed_poisson128.md")
 
 
 def source_digest():
-    """sha256 over the library's CUDA sources and header: a profile's DRAM
-    counters describe the kernel only while this digest is unchanged."""
-    import glob
+    """sha256 over the sources that build the single-system solve kernels and
+    their matrix layout (the repack): a profile's DRAM counters describe the
+    kernel only while this digest is unchanged."""
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_1505_07630_gb300", "csrc", "*.cu*"))
-                   + glob.glob(os.path.join(ROOT, "include", "*.h")))
-    for f in files:
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_1505_07630_gb300", "csrc")
+    for name in ("ldupcg_impl.cuh", "setup.cu", "setup_kernels.cuh", "solve.cu",
+                 "solve_kernels.cuh"):
+        h.update(name.encode())
+        with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
