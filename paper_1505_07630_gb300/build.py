@@ -19,7 +19,10 @@ OBJ_DIR = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIB_DIR, "libldupcg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code is compiled with a*b+c unfused (-ffp-contract=off): gcc fuses by default on aarch64 and
+# cannot without FMA on x86-64, and the AMG setup must build the same hierarchy on both
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+              "-Xcompiler", "-ffp-contract=off",
               "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
 
 

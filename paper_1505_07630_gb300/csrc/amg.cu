@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -53,34 +54,46 @@ struct HCsr {
 };
 
 // both triangles of an LDU matrix, rows sorted, duplicate entries summed
+// (two passes: row lengths, then a fill and a sort of each row's entries)
 HCsr csr_from_ldu(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
                   const double *diag, const double *up, const double *lo) {
-    std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)n);
+    std::vector<int64_t> start((size_t)n + 1, 0);
     for (int64_t i = 0; i < n; ++i)
-        rows[(size_t)i].push_back({(int32_t)i, diag[i]});
+        start[(size_t)i + 1] = 1;
     for (int64_t f = 0; f < nf; ++f) {
-        rows[(size_t)own[f]].push_back({nbr[f], up[f]});
-        rows[(size_t)nbr[f]].push_back({own[f], lo[f]});
+        ++start[(size_t)own[f] + 1];
+        ++start[(size_t)nbr[f] + 1];
+    }
+    for (int64_t i = 0; i < n; ++i)
+        start[(size_t)i + 1] += start[(size_t)i];
+    std::vector<std::pair<int32_t, double>> ent((size_t)start[(size_t)n]);
+    std::vector<int64_t> at(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+        ent[(size_t)at[(size_t)i]++] = {(int32_t)i, diag[i]};
+    for (int64_t f = 0; f < nf; ++f) {
+        ent[(size_t)at[(size_t)own[f]]++] = {nbr[f], up[f]};
+        ent[(size_t)at[(size_t)nbr[f]]++] = {own[f], lo[f]};
     }
     HCsr A;
     A.n = A.m = n;
     A.ptr.assign((size_t)n + 1, 0);
+    A.col.reserve(ent.size());
+    A.val.reserve(ent.size());
     for (int64_t i = 0; i < n; ++i) {
-        auto &r = rows[(size_t)i];
-        std::sort(r.begin(), r.end(),
-                  [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
-                      return a.first < b.first;
-                  });
-        for (size_t k = 0; k < r.size(); ++k) {
-            if (k > 0 && r[k].first == A.col.back()) {
-                A.val.back() += r[k].second;
+        auto b = ent.begin() + start[(size_t)i], e = ent.begin() + start[(size_t)i + 1];
+        // stable: entries of one column keep their face order, so duplicates sum in a fixed order
+        std::stable_sort(b, e, [](const std::pair<int32_t, double> &x,
+                                  const std::pair<int32_t, double> &y) { return x.first < y.first; });
+        const size_t row_begin = A.col.size();
+        for (auto it = b; it != e; ++it) {
+            if (A.col.size() > row_begin && it->first == A.col.back()) {
+                A.val.back() += it->second;
                 continue;
             }
-            A.col.push_back(r[k].first);
-            A.val.push_back(r[k].second);
+            A.col.push_back(it->first);
+            A.val.push_back(it->second);
         }
         A.ptr[(size_t)i + 1] = (int64_t)A.col.size();
-        std::vector<std::pair<int32_t, double>>().swap(r);
     }
     return A;
 }
@@ -222,42 +235,79 @@ HCsr transpose(const HCsr &P) {
 }
 
 // A_c = R A P with R = P^T, one coarse row at a time through a dense
-// accumulator; exact zeros dropped
+// accumulator; exact zeros dropped.  Rows are independent, so blocks of them
+// are formed on several host threads and concatenated in row order: the
+// result does not depend on the thread count.
 HCsr galerkin(const HCsr &A, const HCsr &P, const HCsr &R) {
-    HCsr Ac;
-    Ac.n = Ac.m = P.m;
-    Ac.ptr.assign((size_t)Ac.n + 1, 0);
-    std::vector<double> acc((size_t)Ac.n, 0.0);
-    std::vector<char> used((size_t)Ac.n, 0);
-    std::vector<int32_t> touched;
-    for (int64_t I = 0; I < Ac.n; ++I) {
-        touched.clear();
-        for (int64_t a = R.ptr[(size_t)I]; a < R.ptr[(size_t)I + 1]; ++a) {
-            const int32_t i = R.col[(size_t)a];
-            const double r = R.val[(size_t)a];
-            for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k) {
-                const int32_t j = A.col[(size_t)k];
-                const double ra = r * A.val[(size_t)k];
-                for (int64_t q = P.ptr[(size_t)j]; q < P.ptr[(size_t)j + 1]; ++q) {
-                    const int32_t J = P.col[(size_t)q];
-                    if (!used[(size_t)J]) {
-                        used[(size_t)J] = 1;
-                        touched.push_back(J);
+    const int64_t nc = P.m;
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (nc < 4096)
+        nt = 1;
+    struct Part {
+        std::vector<int64_t> len;
+        std::vector<int32_t> col;
+        std::vector<double> val;
+    };
+    std::vector<Part> parts(nt);
+    auto work = [&](unsigned t) {
+        const int64_t lo = nc * t / nt, hi = nc * (t + 1) / nt;
+        Part &out = parts[t];
+        out.len.assign((size_t)(hi - lo), 0);
+        std::vector<double> acc((size_t)nc, 0.0);
+        std::vector<char> used((size_t)nc, 0);
+        std::vector<int32_t> touched;
+        for (int64_t I = lo; I < hi; ++I) {
+            touched.clear();
+            for (int64_t a = R.ptr[(size_t)I]; a < R.ptr[(size_t)I + 1]; ++a) {
+                const int32_t i = R.col[(size_t)a];
+                const double r = R.val[(size_t)a];
+                for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k) {
+                    const int32_t j = A.col[(size_t)k];
+                    const double ra = r * A.val[(size_t)k];
+                    for (int64_t q = P.ptr[(size_t)j]; q < P.ptr[(size_t)j + 1]; ++q) {
+                        const int32_t J = P.col[(size_t)q];
+                        if (!used[(size_t)J]) {
+                            used[(size_t)J] = 1;
+                            touched.push_back(J);
+                        }
+                        acc[(size_t)J] += ra * P.val[(size_t)q];
                     }
-                    acc[(size_t)J] += ra * P.val[(size_t)q];
                 }
             }
-        }
-        std::sort(touched.begin(), touched.end());
-        for (int32_t J : touched) {
-            if (acc[(size_t)J] != 0.0) {
-                Ac.col.push_back(J);
-                Ac.val.push_back(acc[(size_t)J]);
+            std::sort(touched.begin(), touched.end());
+            int64_t len = 0;
+            for (int32_t J : touched) {
+                if (acc[(size_t)J] != 0.0) {
+                    out.col.push_back(J);
+                    out.val.push_back(acc[(size_t)J]);
+                    ++len;
+                }
+                acc[(size_t)J] = 0.0;
+                used[(size_t)J] = 0;
             }
-            acc[(size_t)J] = 0.0;
-            used[(size_t)J] = 0;
+            out.len[(size_t)(I - lo)] = len;
         }
-        Ac.ptr[(size_t)I + 1] = (int64_t)Ac.col.size();
+    };
+    if (nt == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> pool;
+        for (unsigned t = 0; t < nt; ++t)
+            pool.emplace_back(work, t);
+        for (auto &th : pool)
+            th.join();
+    }
+    HCsr Ac;
+    Ac.n = Ac.m = nc;
+    Ac.ptr.assign((size_t)nc + 1, 0);
+    int64_t row = 0;
+    for (const Part &pt : parts) {
+        for (int64_t len : pt.len) {
+            Ac.ptr[(size_t)row + 1] = Ac.ptr[(size_t)row] + len;
+            ++row;
+        }
+        Ac.col.insert(Ac.col.end(), pt.col.begin(), pt.col.end());
+        Ac.val.insert(Ac.val.end(), pt.val.begin(), pt.val.end());
     }
     return Ac;
 }
@@ -1604,6 +1654,10 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
                         av.push_back(A.val[(size_t)k]);
                     }
                 ap[(size_t)i + 1] = (int)ac.size();
+            }
+            if ((int64_t)ac.size() > INT32_MAX) {
+                free_amg(M);
+                return LDU_ERR_UNSUPPORTED;
             }
             L.a_lpr = lanes ? lanes : lpr_for(A.n, (int64_t)ac.size());
             CKA(upload(&L.a_ptr, ap, nb));

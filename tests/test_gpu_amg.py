@@ -285,3 +285,18 @@ def test_pipelined_full_size_128(pkg):
     _, it2, rr2, st2 = pkg.amg_pipecg_solve(M, dev(s.b), tol=1e-8)
     assert st1 == st2 == 0 and rr2 <= 1e-8 and abs(it1 - it2) <= 1
     M.close()
+
+
+def test_full_size_hierarchy_matches_oracle(pkg, amg):
+    """The 128^3 headline system: every level's row count and the aggregates
+    of the two largest levels bit-exact against the oracle's hierarchy (the
+    library's host code is built with a*b+c unfused, so its rounding is the
+    same on every host)."""
+    s = configs.config2(128)
+    M = pkg.amg_from_system(s)
+    levels, coarse = amg.hierarchy(amg.csr_of(s))
+    assert M.info()["rows"] == [L[0].shape[0] for L in levels] + [coarse.shape[0]]
+    for lev in (0, 1):
+        agg_o, _ = amg.aggregate(levels[lev][0])
+        assert np.array_equal(pkg.ldu_amg_aggregates(M, lev), agg_o), lev
+    M.close()
