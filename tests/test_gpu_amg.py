@@ -300,3 +300,49 @@ def test_full_size_hierarchy_matches_oracle(pkg, amg):
         agg_o, _ = amg.aggregate(levels[lev][0])
         assert np.array_equal(pkg.ldu_amg_aggregates(M, lev), agg_o), lev
     M.close()
+
+
+def test_unsorted_faces_give_the_same_hierarchy(pkg, amg):
+    """Faces need not be sorted: shuffling them (and so the order in which
+    duplicate-free rows are assembled) changes nothing."""
+    s = CASES["lognormal_20x17x13"]()
+    perm = np.random.default_rng(11).permutation(s.nfaces)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), device="cuda", dtype=dt)  # noqa: E731
+    M = pkg.ldu_amg_create(s.n, t(s.owner[perm], torch.int32), t(s.neighbour[perm], torch.int32),
+                           t(s.diag, torch.float64), t(s.upper[perm], torch.float64),
+                           t(s.lower[perm], torch.float64))
+    levels, coarse = amg.hierarchy(amg.csr_of(s))
+    assert M.info()["rows"] == [L[0].shape[0] for L in levels] + [coarse.shape[0]]
+    agg_o, _ = amg.aggregate(levels[0][0])
+    assert np.array_equal(pkg.ldu_amg_aggregates(M, 0), agg_o)
+    M.close()
+
+
+def test_create_validates_like_ldu_create(pkg):
+    s = lc.poisson_box(6, 5, 4)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), device="cuda", dtype=dt)  # noqa: E731
+    own, nbr = s.owner.copy(), s.neighbour.copy()
+    own[3], nbr[3] = nbr[3], own[3]                       # owner > neighbour
+    with pytest.raises(pkg.LduError) as e:
+        pkg.ldu_amg_create(s.n, t(own, torch.int32), t(nbr, torch.int32), t(s.diag, torch.float64),
+                           t(s.upper, torch.float64), t(s.lower, torch.float64))
+    assert e.value.status == -2
+    nbr2 = s.neighbour.copy()
+    nbr2[5] = s.n                                          # index outside [0, n)
+    with pytest.raises(pkg.LduError) as e:
+        pkg.ldu_amg_create(s.n, t(s.owner, torch.int32), t(nbr2, torch.int32),
+                           t(s.diag, torch.float64), t(s.upper, torch.float64),
+                           t(s.lower, torch.float64))
+    assert e.value.status == -2
+    d = s.diag.copy()
+    d[7] = 0.0                                             # non-positive diagonal
+    with pytest.raises(pkg.LduError) as e:
+        pkg.ldu_amg_create(s.n, t(s.owner, torch.int32), t(s.neighbour, torch.int32),
+                           t(d, torch.float64), t(s.upper, torch.float64), t(s.lower, torch.float64))
+    assert e.value.status == -3
+    up = s.upper.copy()
+    up[2] = np.nan                                         # non-finite value
+    with pytest.raises(pkg.LduError) as e:
+        pkg.ldu_amg_create(s.n, t(s.owner, torch.int32), t(s.neighbour, torch.int32),
+                           t(s.diag, torch.float64), t(up, torch.float64), t(s.lower, torch.float64))
+    assert e.value.status == -3
