@@ -373,6 +373,7 @@ struct DSell {
     int n;
     const int *sp, *sw, *col;
     const T *val;
+    const short *c16 = nullptr;   // column - row per slot when every offset fits (else null)
 };
 
 template <typename T>
@@ -488,6 +489,21 @@ __device__ __forceinline__ T sell_row(const DSell<T> &A, int s, int i, F f) {
     const int base = A.sp[s] + i;
     T acc = T(0);
     int k = 0;
+    if (A.c16) {   // 16-bit offsets: 2 instead of 4 bytes per slot (padding slots point at the row)
+        // rows past n in the last slice hold only padding: they gather at row n - 1 (value 0)
+        const int row = min(s * 32 + i, A.n - 1);
+        for (; k + 2 <= w; k += 2) {
+            const int c0 = row + __ldcs(A.c16 + base + k * 32);
+            const int c1 = row + __ldcs(A.c16 + base + (k + 1) * 32);
+            const T v0 = __ldcs(A.val + base + k * 32), v1 = __ldcs(A.val + base + (k + 1) * 32);
+            const T f0 = f(c0), f1 = f(c1);
+            acc = fma(v0, f0, acc);
+            acc = fma(v1, f1, acc);
+        }
+        if (k < w)
+            acc = fma(__ldcs(A.val + base + k * 32), f(row + __ldcs(A.c16 + base + k * 32)), acc);
+        return acc;
+    }
     for (; k + 2 <= w; k += 2) {
         const int c0 = __ldg(A.col + base + k * 32), c1 = __ldg(A.col + base + (k + 1) * 32);
         const T v0 = __ldcs(A.val + base + k * 32), v1 = __ldcs(A.val + base + (k + 1) * 32);
@@ -1071,6 +1087,31 @@ bool sell_of(const HCsr &A, HSell &S) {
     return true;
 }
 
+// the sliced ELL of A's off-diagonal part with its columns as 16-bit offsets
+// from their rows (padding slots: offset 0, the row itself, whose value is
+// 0); false if some offset does not fit
+bool offsets16(const HCsr &A, const HSell &S, std::vector<short> &c16) {
+    c16.assign(S.col.size(), 0);
+    const int64_t ns = (int64_t)S.sw.size();
+    for (int64_t s = 0; s < ns; ++s)
+        for (int i = 0; i < 32; ++i) {
+            const int64_t row = s * 32 + i;
+            if (row >= A.n)
+                break;
+            int len = 0;   // off-diagonal entries of the row: its first len slots
+            for (int64_t e = A.ptr[(size_t)row]; e < A.ptr[(size_t)row + 1]; ++e)
+                len += A.col[(size_t)e] != row;
+            for (int k = 0; k < len; ++k) {
+                const size_t at = (size_t)S.sp[(size_t)s] + (size_t)k * 32 + (size_t)i;
+                const int64_t off = (int64_t)S.col[at] - row;
+                if (off < -32768 || off > 32767)
+                    return false;
+                c16[at] = (short)off;
+            }
+        }
+    return true;
+}
+
 }  // namespace
 
 // the values and vectors of one level in one precision
@@ -1088,6 +1129,7 @@ struct amg_level {
     // A's off-diagonal part: sliced ELL on level 0 (a_sp, a_sw), CSR on
     // coarser levels (a_ptr)
     int *a_sp = nullptr, *a_sw = nullptr, *a_ptr = nullptr, *a_col = nullptr;
+    short *a_c16 = nullptr;                   // sliced ELL's columns as offsets from the row (float cycle)
     int *p_ptr = nullptr, *p_col = nullptr;   // P: n x n_next
     int *r_ptr = nullptr, *r_col = nullptr;   // R = P^T: n_next x n
     int a_lpr = 1, p_lpr = 1, r_lpr = 1;      // lanes per row of the CSR reads
@@ -1099,7 +1141,10 @@ struct amg_level {
     template <typename T>
     const LevelVals<T> &v() const;
     template <typename T>
-    DSell<T> A() const { return DSell<T>{(int)n, a_sp, a_sw, a_col, v<T>().a_val}; }
+    DSell<T> A() const {
+        return DSell<T>{(int)n, a_sp, a_sw, a_col, v<T>().a_val,
+                        std::is_same<T, float>::value ? a_c16 : nullptr};
+    }
     template <typename T>
     DCsr<T> Acsr() const { return DCsr<T>{(int)n, a_ptr, a_col, v<T>().a_val}; }
     template <typename T>
@@ -1166,7 +1211,7 @@ void free_amg(ldu_amg *M) {
     if (!M)
         return;
     for (auto &L : M->lev) {
-        void *ptrs[] = {L.a_sp, L.a_sw, L.a_ptr, L.a_col, L.p_ptr, L.p_col, L.r_ptr, L.r_col};
+        void *ptrs[] = {L.a_sp, L.a_sw, L.a_ptr, L.a_col, L.a_c16, L.p_ptr, L.p_col, L.r_ptr, L.r_col};
         for (void *p : ptrs)
             if (p)
                 cudaFree(p);
@@ -1640,6 +1685,9 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
             CKA(upload(&L.a_sp, S.sp, nb));
             CKA(upload(&L.a_sw, S.sw, nb));
             CKA(upload(&L.a_col, S.col, nb));
+            std::vector<short> c16;
+            if (offsets16(A, S, c16))
+                CKA(upload(&L.a_c16, c16, nb));
             CKA(upload2(&L.v64.a_val, &L.v32.a_val, S.val, nb));
         } else {
             // off-diagonal CSR of a coarse level
