@@ -413,11 +413,16 @@ typedef struct amg_opts {
 
 /* Build the hierarchy of an LDU matrix.  n, nFaces, owner, neighbour,
  * diag, upper, lower: as ldu_create (device arrays, copied to the host and
- * validated there).  aopt: host, may be NULL.  Every level stores A's
- * off-diagonal part in sliced ELL with 32-row slices, its diagonal, P as CSR
- * and R = P^T as CSR.  Synchronises stream.  Errors as ldu_create; NOT_SPD
- * if the coarsest matrix is singular; UNSUPPORTED if coarsening stops above
- * 4096 rows. */
+ * validated there; the hierarchy uses both triangles, the solvers need a
+ * symmetric positive definite A).  aopt: host, may be NULL.  The fine level
+ * stores A's off-diagonal part in sliced ELL with 32-row slices (plus 16-bit
+ * column offsets from the row when every offset fits), coarse levels in CSR;
+ * every level keeps its diagonal and w/diagonal, P and R = P^T in CSR, all
+ * values in double and in float.  The Galerkin products run on up to 16 host
+ * threads (the result does not depend on their number).  Synchronises
+ * stream.  Errors as ldu_create; NOT_SPD if the coarsest matrix is singular;
+ * UNSUPPORTED if coarsening stops above 4096 rows or a level's entries
+ * exceed int32 indexing. */
 int ldu_amg_create(int64_t n, int64_t nFaces, const int32_t *owner, const int32_t *neighbour,
                    const double *diag, const double *upper, const double *lower,
                    const amg_opts *aopt, ldu_stream_t stream, ldu_amg **out);
@@ -467,7 +472,8 @@ int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit,
  * recursive residual and confirms with the true one (a disagreement
  * restarts the recurrences from it).  Arguments, outputs and errors as
  * amg_pcg_solve (FP64 only).  Allocates seven work vectors on a hierarchy's
- * first call.  Synchronises stream. */
+ * first call; one iteration is captured and replayed as a CUDA graph as in
+ * amg_pcg_solve.  Synchronises stream. */
 int amg_pipecg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
                      double *relres, ldu_stream_t stream);
 
