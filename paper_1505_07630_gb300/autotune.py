@@ -52,11 +52,25 @@ def _store(key, value):
     os.replace(tmp, CACHE)
 
 
+_FLUSH = None
+
+
+def _flush_l2():
+    """Overwrite a buffer twice the size of the 129 MB L2, as the benchmark
+    does before every timed solve, so that candidates are ranked under the
+    conditions they are measured in."""
+    global _FLUSH
+    if _FLUSH is None:
+        _FLUSH = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    _FLUSH.fill_(1.0)
+
+
 def _time(call, repeats):
     call()                                   # warm-up
     torch.cuda.synchronize()
     best = float("inf")
     for _ in range(repeats):
+        _flush_l2()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -71,7 +85,7 @@ def _time(call, repeats):
 RR_RULES = ((16, 0.3), (16, 0.2), (14, 0.0), (12, 0.0), (20, 0.3))
 
 
-def tune_single(system, precision="mixed", tol=1e-8, repeats=2, use_cache=True,
+def tune_single(system, precision="mixed", tol=1e-8, repeats=3, use_cache=True,
                 slice_rows=SLICE_ROWS, **solve_kw):
     """Best slice height (and, for the mixed solve, replacement period and
     tau) for pcg_solve ('pcg') / pipecg_solve ('fp64', 'mixed') on this
@@ -112,7 +126,7 @@ def tune_single(system, precision="mixed", tol=1e-8, repeats=2, use_cache=True,
     return best
 
 
-def tune_batched(systems, precision="mixed", tol=1e-8, repeats=2, use_cache=True, **solve_kw):
+def tune_batched(systems, precision="mixed", tol=1e-8, repeats=3, use_cache=True, **solve_kw):
     """Best (slice height, team schedule) for pcg_solve_batched on this batch."""
     sizes = [s.n for s in systems]
     faces = [s.nfaces for s in systems]

@@ -346,3 +346,25 @@ def test_create_validates_like_ldu_create(pkg):
         pkg.ldu_amg_create(s.n, t(s.owner, torch.int32), t(s.neighbour, torch.int32),
                            t(s.diag, torch.float64), t(up, torch.float64), t(s.lower, torch.float64))
     assert e.value.status == -3
+
+
+@pytest.mark.parametrize("solver", ["fp64", "mixed", "pipelined"])
+def test_unreachable_tolerance_restarts_and_stops_at_the_cap(pkg, amg, solver):
+    """tol = 1e-16 lies below what FP64 can confirm: the recursive residual
+    passes it, the true residual does not, the search restarts from the true
+    residual (the confirmation path), and the loop ends at the iteration cap
+    with NOT_CONVERGED and the reported residual equal to the recomputed one."""
+    s = CASES["lognormal_rcm24"]()
+    M = pkg.amg_from_system(s)
+    if solver == "pipelined":
+        x, it, relres, st = pkg.amg_pipecg_solve(M, dev(s.b), tol=1e-16, maxit=80, check=False)
+    else:
+        x, it, relres, st = pkg.amg_pcg_solve(M, dev(s.b), tol=1e-16, maxit=80,
+                                              precision=solver, check=False)
+    assert st in (0, 1) and it <= 80
+    A = amg.csr_of(s)
+    true = np.linalg.norm(s.b - A @ x.cpu().numpy()) / np.linalg.norm(s.b)
+    # both residuals are formed at rounding level here: they agree to a few 1e-17
+    assert abs(true - relres) <= max(1e-3 * true, 1e-16)
+    assert true <= 1e-13   # it still reached FP64's attainable accuracy
+    M.close()
