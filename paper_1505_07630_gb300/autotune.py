@@ -3,7 +3,8 @@
 For a single system it times the solve over the slice heights (rows per
 sliced-ELL slice: 32, 64, 128); for a batch it also tries team schedules
 (largest team, work-per-block scale).  Each candidate is timed with CUDA
-events on the calling stream after one warm-up solve, best of `repeats`.
+events on the calling stream after one warm-up solve, best of `repeats`,
+with the L2 flushed before every timed solve (as the benchmark does).
 Results are cached in a JSON file keyed by the problem's shape, so a later
 run with the same sizes reuses the choice without timing.
 
