@@ -366,5 +366,8 @@ def test_unreachable_tolerance_restarts_and_stops_at_the_cap(pkg, amg, solver):
     true = np.linalg.norm(s.b - A @ x.cpu().numpy()) / np.linalg.norm(s.b)
     # both residuals are formed at rounding level here: they agree to a few 1e-17
     assert abs(true - relres) <= max(1e-3 * true, 1e-16)
-    assert true <= 1e-13   # it still reached FP64's attainable accuracy
+    # attainable accuracy: PCG reaches FP64's; the pipelined recurrences (four
+    # coupled updates, no periodic replacement) drift from the true residual
+    # to about 1e-10 before the confirmation restarts them
+    assert true <= (1e-9 if solver == "pipelined" else 1e-13)
     M.close()
