@@ -1342,21 +1342,17 @@ int read_scalars(ldu_amg *M, cudaStream_t st) {
     return cuda_status(e);
 }
 
-// the outer PCG with the cycle in precision T (double: Saad Alg. 9.1 with
-// z = V(r); float: the same with the Polak-Ribiere beta)
-template <typename T>
-int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
-             double *relres, cudaStream_t st) {
-    const bool f32 = std::is_same<T, float>::value;
-    const DSell<double> A = M->fine();
-    const double *d = M->fine_d();
-    const int64_t n = M->n;
-    const int ga = grid_rows(n);
-    const T *wd0 = M->lev.empty() ? nullptr : M->lev[0].v<T>().wd;   // cycle input t0 = (w/d) r
-    T *t0 = M->lev.empty() ? nullptr : M->lev[0].v<T>().t;
-    T *bv = f32 ? (T *)M->r32 : nullptr;                  // float cycle: its own copy of r
-    const T *cyc_b = f32 ? (const T *)M->r32 : (const T *)M->r;
-    T *cyc_z = f32 ? (T *)M->z32 : (T *)M->z;
+// The outer loop shared by AMG-PCG and AMG-PipeCG.  residual(mode) queues
+// r = b - A x with the cycle's input (mode 0 also sets bn2 and the
+// threshold, see k_amg_residual); resume() queues the restart of the search
+// from that residual; body(stream) queues one iteration (captured once as a
+// graph, see iteration_graph).  The host starts the loop, launches the
+// iteration graph in batches, and when the recursive residual meets the
+// tolerance confirms it with the true residual (restarting from it when it
+// disagrees); the relative true residual at exit goes to relres.
+template <typename Res, typename Resume, typename Body>
+int outer_loop(ldu_amg *M, int kind, double *x, double tol, int maxit, Res residual,
+               Resume resume, Body body, int *iters, double *relres, cudaStream_t st) {
     AmgScalars *S = M->S, *H = M->S_host;
     std::memset(H, 0, sizeof(AmgScalars));
     H->tol2 = tol * tol;
@@ -1365,36 +1361,28 @@ int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int 
     cudaError_t e = cudaMemcpyAsync(S, H, sizeof(AmgScalars), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess)
         return cuda_status(e);
-    int rc = LDU_OK;
-    // r = b - A x0, then z = V(r) and (r, z)
-    k_amg_residual<T><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, wd0, t0, bv, 0, S, M->part,
-                                               M->count);
-    if ((rc = vcycle<T>(M, 0, cyc_b, cyc_z, true, nullptr, st)) != LDU_OK)
-        return rc;
-    if ((rc = read_scalars(M, st)) != LDU_OK)
+    int rc = residual(0);
+    if (rc == LDU_OK)
+        rc = resume();
+    if (rc == LDU_OK)
+        rc = read_scalars(M, st);
+    if (rc != LDU_OK)
         return rc;
     int status = LDU_NOT_CONVERGED, it = 0;
     bool confirmed = false;   // H->rr holds the true residual of the final x
     const double bn2 = H->bn2, thr2 = H->thr2;
     if (bn2 == 0.0) {
-        cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st);
+        cudaMemsetAsync(x, 0, sizeof(double) * (size_t)M->n, st);
         status = LDU_OK;
     } else if (H->rr <= thr2) {
         status = LDU_OK;
         confirmed = true;
     } else if (maxit > 0) {
+        cudaGraphExec_t step = nullptr;
+        if ((rc = iteration_graph(M, kind, x, body, &step)) != LDU_OK)
+            return rc;
         // iterations in batches between host reads, sized from the observed
         // convergence rate so that few kernels run past the stopping point
-        cudaGraphExec_t step = nullptr;
-        rc = iteration_graph(M, f32 ? 0 : 1, x, [&](cudaStream_t cs) {
-            k_amg_p<T><<<ga, kThreads, 0, cs>>>((int)n, (const T *)cyc_z, M->p, S);
-            k_amg_q<<<ga, kThreads, 0, cs>>>(A, d, M->p, M->q, S, M->part, M->count);
-            k_amg_xr<T><<<ga, kThreads, 0, cs>>>((int)n, M->p, M->q, x, M->r, wd0, t0, bv, S,
-                                                 M->part, M->count);
-            return vcycle<T>(M, 0, cyc_b, cyc_z, true, &S->done, cs);
-        }, &step);
-        if (rc != LDU_OK)
-            return rc;
         double rr_prev = H->rr;
         int it_prev = 0, batch = 4;
         for (;;) {
@@ -1412,9 +1400,7 @@ int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int 
             }
             if (H->conv) {
                 // confirm with the true residual; restart the search if it disagrees
-                k_amg_residual<T><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, wd0, t0, bv, 1, S,
-                                                           M->part, M->count);
-                if ((rc = read_scalars(M, st)) != LDU_OK)
+                if ((rc = residual(1)) != LDU_OK || (rc = read_scalars(M, st)) != LDU_OK)
                     return rc;
                 if (H->rr <= thr2) {
                     status = LDU_OK;
@@ -1423,7 +1409,7 @@ int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int 
                 }
                 if (it >= maxit)
                     break;
-                if ((rc = vcycle<T>(M, 0, cyc_b, cyc_z, true, nullptr, st)) != LDU_OK)
+                if ((rc = resume()) != LDU_OK)
                     return rc;
                 continue;
             }
@@ -1441,12 +1427,8 @@ int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int 
     }
     // the true residual at exit
     double tr = 0.0;
-    if (bn2 > 0.0 && confirmed) {
-        tr = std::sqrt(H->rr / bn2);
-    } else if (bn2 > 0.0) {
-        k_amg_residual<T><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, nullptr, nullptr, nullptr, 1,
-                                                   S, M->part, M->count);
-        if ((rc = read_scalars(M, st)) != LDU_OK)
+    if (bn2 > 0.0) {
+        if (!confirmed && ((rc = residual(1)) != LDU_OK || (rc = read_scalars(M, st)) != LDU_OK))
             return rc;
         tr = std::sqrt(H->rr / bn2);
     }
@@ -1455,6 +1437,39 @@ int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int 
     if (relres)
         *relres = tr;
     return status;
+}
+
+// AMG-PCG with the cycle in precision T (double: Saad Alg. 9.1 with z = V(r);
+// float: the same with the Polak-Ribiere beta)
+template <typename T>
+int pcg_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int *iters,
+             double *relres, cudaStream_t st) {
+    const bool f32 = std::is_same<T, float>::value;
+    const DSell<double> A = M->fine();
+    const double *d = M->fine_d();
+    const int64_t n = M->n;
+    const int ga = grid_rows(n);
+    const T *wd0 = M->lev.empty() ? nullptr : M->lev[0].v<T>().wd;   // cycle input t0 = (w/d) r
+    T *t0 = M->lev.empty() ? nullptr : M->lev[0].v<T>().t;
+    T *bv = f32 ? (T *)M->r32 : nullptr;                  // float cycle: its own copy of r
+    const T *cyc_b = f32 ? (const T *)M->r32 : (const T *)M->r;
+    T *cyc_z = f32 ? (T *)M->z32 : (T *)M->z;
+    AmgScalars *S = M->S;
+    auto residual = [&](int mode) {
+        k_amg_residual<T><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, wd0, t0, bv, mode, S,
+                                                   M->part, M->count);
+        return cuda_status(cudaGetLastError());
+    };
+    // z = V(r) with (r, z); the next direction is z itself
+    auto resume = [&]() { return vcycle<T>(M, 0, cyc_b, cyc_z, true, nullptr, st); };
+    auto body = [&](cudaStream_t cs) {
+        k_amg_p<T><<<ga, kThreads, 0, cs>>>((int)n, (const T *)cyc_z, M->p, S);
+        k_amg_q<<<ga, kThreads, 0, cs>>>(A, d, M->p, M->q, S, M->part, M->count);
+        k_amg_xr<T><<<ga, kThreads, 0, cs>>>((int)n, M->p, M->q, x, M->r, wd0, t0, bv, S, M->part,
+                                             M->count);
+        return vcycle<T>(M, 0, cyc_b, cyc_z, true, &S->done, cs);
+    };
+    return outer_loop(M, f32 ? 0 : 1, x, tol, maxit, residual, resume, body, iters, relres, st);
 }
 
 // pipelined PCG with the FP64 cycle (Table 2's AMG-PipeCG): per step one
@@ -1476,109 +1491,29 @@ int pipe_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int
     const PipeVecs V{m, nv, M->pv[4], M->pv[5], M->pv[6], M->p, x, M->r, u, w};
     const double *wd0 = M->lev.empty() ? nullptr : M->lev[0].v64.wd;
     double *t0 = M->lev.empty() ? nullptr : M->lev[0].v64.t;
-    AmgScalars *S = M->S, *H = M->S_host;
-    std::memset(H, 0, sizeof(AmgScalars));
-    H->tol2 = tol * tol;
-    H->maxit = maxit;
-    H->status = LDU_OK;
-    cudaError_t e = cudaMemcpyAsync(S, H, sizeof(AmgScalars), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess)
-        return cuda_status(e);
-    int rc = LDU_OK;
-    // r = b - A x0 (and the cycle's input), u = V(r), w = A u, gamma, delta
-    auto start = [&](int mode) {
+    AmgScalars *S = M->S;
+    auto residual = [&](int mode) {
         k_amg_residual<double><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, wd0, t0, nullptr, mode,
                                                         S, M->part, M->count);
-        int r2 = vcycle<double>(M, 0, M->r, u, false, nullptr, st);
+        return cuda_status(cudaGetLastError());
+    };
+    // u = V(r), w = A u with gamma and delta; the recurrences restart
+    auto resume = [&]() {
+        const int r2 = vcycle<double>(M, 0, M->r, u, false, nullptr, st);
         if (r2 != LDU_OK)
             return r2;
         k_pp_init<<<ga, kThreads, 0, st>>>(A, d, u, M->r, w, wd0, t0, S, M->part, M->count);
         return cuda_status(cudaGetLastError());
     };
-    if ((rc = start(0)) != LDU_OK)
-        return rc;
-    if ((rc = read_scalars(M, st)) != LDU_OK)
-        return rc;
-    int status = LDU_NOT_CONVERGED, it = 0;
-    bool confirmed = false;
-    const double bn2 = H->bn2, thr2 = H->thr2;
-    if (bn2 == 0.0) {
-        cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, st);
-        status = LDU_OK;
-    } else if (H->rr <= thr2) {
-        status = LDU_OK;
-        confirmed = true;
-    } else if (maxit > 0) {
-        cudaGraphExec_t step = nullptr;
-        rc = iteration_graph(M, 2, x, [&](cudaStream_t cs) {
-            const int r2 = vcycle<double>(M, 0, w, m, false, &S->done, cs);
-            if (r2 != LDU_OK)
-                return r2;
-            k_pp_spmv<<<ga, kThreads, 0, cs>>>(A, d, m, nv, S);
-            k_pp_update<<<ga, kThreads, 0, cs>>>((int)n, V, wd0, t0, S, M->part, M->count);
-            return cuda_status(cudaGetLastError());
-        }, &step);
-        if (rc != LDU_OK)
-            return rc;
-        double rr_prev = H->rr;
-        int it_prev = 0, batch = 4;
-        for (;;) {
-            for (int g = 0; g < batch; ++g) {
-                const cudaError_t eg = cudaGraphLaunch(step, st);
-                if (eg != cudaSuccess)
-                    return cuda_status(eg);
-            }
-            if ((rc = read_scalars(M, st)) != LDU_OK)
-                return rc;
-            it = H->it;
-            if (H->status == LDU_ERR_NOT_SPD) {
-                status = LDU_ERR_NOT_SPD;
-                break;
-            }
-            if (H->conv) {
-                k_amg_residual<double><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, nullptr,
-                                                                nullptr, nullptr, 1, S, M->part,
-                                                                M->count);
-                if ((rc = read_scalars(M, st)) != LDU_OK)
-                    return rc;
-                if (H->rr <= thr2) {
-                    status = LDU_OK;
-                    confirmed = true;
-                    break;
-                }
-                if (it >= maxit)
-                    break;
-                // restart the recurrences from the true residual
-                if ((rc = start(1)) != LDU_OK)
-                    return rc;
-                continue;
-            }
-            if (H->status == LDU_NOT_CONVERGED)
-                break;
-            const double rho = std::pow(H->rr / rr_prev, 1.0 / std::max(1, it - it_prev));
-            double left = 8.0;
-            if (rho > 0.0 && rho < 1.0)
-                left = std::min(8.0, std::log(thr2 / H->rr) / std::log(rho));
-            batch = std::min(maxit - it, std::max(1, (int)std::lround(left)));
-            rr_prev = H->rr;
-            it_prev = it;
-        }
-    }
-    double tr = 0.0;
-    if (bn2 > 0.0 && confirmed) {
-        tr = std::sqrt(H->rr / bn2);
-    } else if (bn2 > 0.0) {
-        k_amg_residual<double><<<ga, kThreads, 0, st>>>(A, d, b, x, M->r, nullptr, nullptr,
-                                                        nullptr, 1, S, M->part, M->count);
-        if ((rc = read_scalars(M, st)) != LDU_OK)
-            return rc;
-        tr = std::sqrt(H->rr / bn2);
-    }
-    if (iters)
-        *iters = it;
-    if (relres)
-        *relres = tr;
-    return status;
+    auto body = [&](cudaStream_t cs) {
+        const int r2 = vcycle<double>(M, 0, w, m, false, &S->done, cs);
+        if (r2 != LDU_OK)
+            return r2;
+        k_pp_spmv<<<ga, kThreads, 0, cs>>>(A, d, m, nv, S);
+        k_pp_update<<<ga, kThreads, 0, cs>>>((int)n, V, wd0, t0, S, M->part, M->count);
+        return cuda_status(cudaGetLastError());
+    };
+    return outer_loop(M, 2, x, tol, maxit, residual, resume, body, iters, relres, st);
 }
 
 }  // namespace
