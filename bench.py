@@ -220,6 +220,11 @@ def oracle_sample(sys_, iters_cap):
     return dt / max(r.iters, 1), r
 
 
+# the workload both arms solve: the 128^3 lognormal Poisson system to relative residual 1e-8
+WORKLOAD = ("poisson {size}^3 lognormal(0,1) k, harmonic faces, random+RCM order, Dirichlet "
+            "x-walls; Jacobi-preconditioned CG to 1e-8")
+
+
 def run_reference(args):
     ranks = Ranks()
     if ranks.rank != 0:
@@ -244,9 +249,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"poisson {args.size}^3 lognormal(0,1) k, random+RCM order, "
-                               "Jacobi-PCG to 1e-8 (oracle, plain C)", "cells": s.n,
-                   "faces": s.nfaces},
+        "config": {"workload": WORKLOAD.format(size=args.size), "cells": s.n, "faces": s.nfaces,
+                   "solver": "FP64 Jacobi-PCG, the oracle (plain C, one host core)"},
         "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -449,8 +453,8 @@ def run_ours(args):
         "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"poisson {args.size}^3 lognormal(0,1) k, harmonic faces, random+RCM "
-                               "order, Dirichlet x-walls; mixed pipelined Jacobi-PCG to 1e-8",
+        "config": {"workload": WORKLOAD.format(size=args.size),
+                   "solver": "mixed pipelined Jacobi-PCG (libldupcg, k_mixed)",
                    "cells": n, "faces": F, "slice_rows": A.info()["slice_rows"],
                    "blocks_per_sm": args.blocks_per_sm, "staging": args.staging,
                    "grid_blocks": grid["grid_blocks"], "block_threads": grid["block_threads"],
