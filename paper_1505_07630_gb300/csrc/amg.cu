@@ -396,7 +396,8 @@ struct AmgScalars {
 
 constexpr int kWarps = 8;                 // warps (slices) per block
 constexpr int kThreads = kWarps * 32;
-constexpr int kMaxBlocks = 152 * 8;       // grid cap: 8 resident blocks on each of 152 SMs
+constexpr int kBlocksPerSm = 8;           // every kernel is built to keep 8 blocks resident (32 registers)
+constexpr int kMaxBlocks = 152 * kBlocksPerSm;   // grid cap: one wave of 8 blocks on each of 152 SMs
 
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1)
@@ -558,7 +559,7 @@ struct Row3 {
 // the residual after pre-smoothing from zero, t = (w/d) b having been
 // written by the producer of b:  r = b - A t
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_pre(DSell<T> A, const T *__restrict__ d,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_pre(DSell<T> A, const T *__restrict__ d,
                                                       const T *__restrict__ b,
                                                       const T *__restrict__ t,
                                                       T *__restrict__ r, const int *skip) {
@@ -574,7 +575,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_pre(DSell<T> A, const T *__res
 }
 
 template <int LPR, typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_pre_csr(DCsr<T> A, const T *__restrict__ d,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_pre_csr(DCsr<T> A, const T *__restrict__ d,
                                                           const T *__restrict__ b,
                                                           const T *__restrict__ t,
                                                           T *__restrict__ r, const int *skip) {
@@ -591,7 +592,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_pre_csr(DCsr<T> A, const T *__
 // scalars: each thread sums its few rows in T, the grid in double (a float
 // cycle's dot products need no more: the float z carries 1e-7 already)
 template <typename T, bool DOT, bool PR>
-__global__ void __launch_bounds__(kThreads) k_amg_post(DSell<T> A, const T *__restrict__ d,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_post(DSell<T> A, const T *__restrict__ d,
                                                        const T *__restrict__ wd,
                                                        const T *__restrict__ b,
                                                        const T *__restrict__ t,
@@ -624,7 +625,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_post(DSell<T> A, const T *__re
 }
 
 template <int LPR, typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_post_csr(DCsr<T> A, const T *__restrict__ d,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_post_csr(DCsr<T> A, const T *__restrict__ d,
                                                            const T *__restrict__ wd,
                                                            const T *__restrict__ b,
                                                            const T *__restrict__ t,
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_post_csr(DCsr<T> A, const T *_
 // b_c = R r, and t_c = (w/d)_c b_c for the coarse level's pre-smoothing
 // (wdc null when the coarse level is the coarsest)
 template <int LPR, typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_restrict(DCsr<T> R, const T *__restrict__ r,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_restrict(DCsr<T> R, const T *__restrict__ r,
                                                            const T *__restrict__ wdc,
                                                            T *__restrict__ bc, T *__restrict__ tc,
                                                            const int *skip) {
@@ -656,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_restrict(DCsr<T> R, const T *_
 
 // t += P x_c
 template <int LPR, typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_prolong(DCsr<T> P, const T *__restrict__ xc,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_prolong(DCsr<T> P, const T *__restrict__ xc,
                                                           T *__restrict__ t, const int *skip) {
     if (skip && *skip)
         return;
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_prolong(DCsr<T> P, const T *__
 // x = Minv b on the coarsest level, one warp per row; with DOT (a system
 // that is its own coarsest level) also the outer PCG's dot products
 template <typename T, bool DOT, bool PR>
-__global__ void __launch_bounds__(kThreads) k_amg_dense(int n, const T *__restrict__ Minv,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_dense(int n, const T *__restrict__ Minv,
                                                         const T *__restrict__ b,
                                                         T *__restrict__ x, const int *skip,
                                                         AmgScalars *S, double *part,
@@ -710,7 +711,7 @@ __device__ __forceinline__ void cycle_input(int i, double bi, const T *wd, T *t,
 
 // stand-alone cycle input
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_scale(int n, const T *__restrict__ wd,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_scale(int n, const T *__restrict__ wd,
                                                         const T *__restrict__ b,
                                                         T *__restrict__ t) {
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads)
@@ -721,7 +722,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_scale(int n, const T *__restri
 // from r; mode 0 starts a solve (bn2, thr2, rr), mode 1 measures the true
 // residual (rr only); both make the next direction restart
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_residual(DSell<double> A,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_residual(DSell<double> A,
                                                            const double *__restrict__ d,
                                                            const double *__restrict__ b,
                                                            const double *__restrict__ x,
@@ -759,7 +760,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_residual(DSell<double> A,
 
 // p = z + beta p, or p = z after a restart
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_p(int n, const T *__restrict__ z,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_p(int n, const T *__restrict__ z,
                                                     double *__restrict__ p,
                                                     const AmgScalars *S) {
     if (S->done)
@@ -771,7 +772,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_p(int n, const T *__restrict__
 }
 
 // q = A p with (p, q) reduced into alpha
-__global__ void __launch_bounds__(kThreads) k_amg_q(DSell<double> A, const double *__restrict__ d,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_q(DSell<double> A, const double *__restrict__ d,
                                                     const double *__restrict__ p,
                                                     double *__restrict__ q, AmgScalars *S,
                                                     double *part, unsigned *count) {
@@ -806,7 +807,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_q(DSell<double> A, const doubl
 // the iteration is counted and the loop stops when the recursive residual
 // meets the tolerance or maxit iterations have run
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_amg_xr(int n, const double *__restrict__ p,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_amg_xr(int n, const double *__restrict__ p,
                                                      const double *__restrict__ q,
                                                      double *__restrict__ x,
                                                      double *__restrict__ r,
@@ -842,7 +843,7 @@ __global__ void __launch_bounds__(kThreads) k_amg_xr(int n, const double *__rest
 
 // w = A u with gamma = (r, u) and delta = (w, u); the cycle's next input
 // t0 = (w/d) w; the recurrences restart (beta = 0) at the next update
-__global__ void __launch_bounds__(kThreads) k_pp_init(DSell<double> A, const double *__restrict__ d,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_pp_init(DSell<double> A, const double *__restrict__ d,
                                                       const double *__restrict__ u,
                                                       const double *__restrict__ r,
                                                       double *__restrict__ w,
@@ -875,7 +876,7 @@ __global__ void __launch_bounds__(kThreads) k_pp_init(DSell<double> A, const dou
 }
 
 // y = A x on the fine level (FP64)
-__global__ void __launch_bounds__(kThreads) k_pp_spmv(DSell<double> A, const double *__restrict__ d,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) k_pp_spmv(DSell<double> A, const double *__restrict__ d,
                                                       const double *__restrict__ x,
                                                       double *__restrict__ y,
                                                       const AmgScalars *S) {
@@ -899,7 +900,8 @@ struct PipeVecs {
 // thread forms the same values), the eight recurrences, the cycle's next
 // input t0 = (w/d) w, and (r, u), (w, u), (r, r) for the next step; the
 // last block counts the step and tests convergence
-__global__ void __launch_bounds__(kThreads) k_pp_update(int n, PipeVecs V,
+constexpr int kUpdateBlocksPerSm = 6;   // the eight-vector update needs more than 32 registers
+__global__ void __launch_bounds__(kThreads, kUpdateBlocksPerSm) k_pp_update(int n, PipeVecs V,
                                                         const double *__restrict__ wd,
                                                         double *__restrict__ t, AmgScalars *S,
                                                         double *part, unsigned *count) {
@@ -1510,7 +1512,8 @@ int pipe_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int
         if (r2 != LDU_OK)
             return r2;
         k_pp_spmv<<<ga, kThreads, 0, cs>>>(A, d, m, nv, S);
-        k_pp_update<<<ga, kThreads, 0, cs>>>((int)n, V, wd0, t0, S, M->part, M->count);
+        k_pp_update<<<std::min(ga, 152 * kUpdateBlocksPerSm), kThreads, 0, cs>>>(
+            (int)n, V, wd0, t0, S, M->part, M->count);
         return cuda_status(cudaGetLastError());
     };
     return outer_loop(M, 2, x, tol, maxit, residual, resume, body, iters, relres, st);
