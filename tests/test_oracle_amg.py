@@ -141,3 +141,28 @@ def test_pipelined_iterates_equal_pcg_iterates():
         x1 = amg.amg_pcg(s, tol=1e-30, maxit=k).x
         x2 = amg.amg_pipecg(s, tol=1e-30, maxit=k).x
         assert np.max(np.abs(x1 - x2)) <= 1e-10 * np.max(np.abs(x1)), k
+
+
+def test_two_grid_error_propagator():
+    """With one prolongator and an exact coarse solve, the V(1,1) cycle's
+    error propagator I - B A (B the cycle as an operator, probed on unit
+    vectors) is the textbook product (I - S A)(I - P A_c^-1 P^T A)(I - S A)
+    with S = w D^-1: pre-smoothing, exact coarse correction, post-smoothing."""
+    s = lc.poisson_box(9, 8, 7, diffusivity="lognormal", seed=13)
+    A = amg.csr_of(s)
+    levels, coarse = amg.hierarchy(A, max_coarse=200, max_levels=1)
+    assert len(levels) == 1
+    Af, P, w = levels[0]
+    Ad = Af.toarray()
+    Pd = P.toarray()
+    n = s.n
+    B = np.column_stack([amg.vcycle(levels, coarse, e) for e in np.eye(n)])
+    S = w * np.diag(1.0 / np.diag(Ad))
+    I = np.eye(n)
+    Ac = Pd.T @ Ad @ Pd
+    assert np.allclose(Ac, coarse, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
+    E = (I - S @ Ad) @ (I - Pd @ np.linalg.solve(Ac, Pd.T @ Ad)) @ (I - S @ Ad)
+    assert np.max(np.abs((I - B @ Ad) - E)) <= 1e-10
+    # and the two-grid method contracts in the energy norm
+    L = np.linalg.cholesky(Ad)
+    assert np.linalg.norm(L.T @ E @ np.linalg.inv(L.T), 2) < 1.0
