@@ -106,3 +106,23 @@ def test_warm_start_from_previous_pressure():
     cold = piso.pressure_step(s, s.coef, phi2, tol=1e-10)
     assert warm.iters < cold.iters
     assert np.max(np.abs(warm.p - cold.p)) <= 1e-6 * np.max(np.abs(cold.p))
+
+
+def test_stage_is_the_weighted_projection():
+    """The corrected flux is the closed-form projection of phi* onto the
+    divergence-free fluxes in the 1/c-weighted face product,
+    phi = (I - C D^T (D C D^T)^+ D) phi*, with D the face-to-cell divergence
+    matrix and C = diag(c): computed densely here, independently of the
+    stage's solve-and-correct steps."""
+    s, phi = pressure_case(6)
+    F, n = s.owner.shape[0], s.n
+    D = np.zeros((n, F))
+    D[s.owner, np.arange(F)] = 1.0
+    D[s.neighbour, np.arange(F)] = -1.0
+    C = np.diag(s.coef)
+    L = D @ C @ D.T                      # the unpinned Laplacian (singular: constants)
+    # L^+ (D phi) by least squares (D phi sums to zero, so it lies in L's range)
+    proj = phi - C @ D.T @ np.linalg.lstsq(L, D @ phi, rcond=None)[0]
+    r = piso.pressure_step(s, s.coef, phi, tol=1e-13)
+    assert np.max(np.abs(r.phi - proj)) <= 1e-9 * np.max(np.abs(proj))
+    assert np.max(np.abs(D @ proj)) <= 1e-10 * np.max(np.abs(D @ phi))
