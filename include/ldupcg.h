@@ -486,11 +486,17 @@ int amg_pipecg_solve(ldu_amg *M, const double *b, double *x, double tol, int max
  * the same layout and launch shape, so the result equals pcg_solve's on a
  * default handle.  All intermediate data live in one fixed-size __device__
  * array (8,130,816 bytes (7.75 MiB)) that every GPU loading the library holds until the
- * process exits; on each device the first call looks up its address
- * (cudaGetSymbolAddress) with that device current.
- *   n <= 32768 cells, nFaces <= 131072, at most 262144 stored off-diagonal
- *   slots (8 per row on average, padding included); larger inputs return
- *   LDU_ERR_UNSUPPORTED without doing any work.
+ * process exits.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process, so that first call should come before any stream capture,
+ * and the entry point must not be used again after a cudaDeviceReset in the
+ * same process.
+ *   n <= 32768 cells and nFaces <= 131072: larger inputs return
+ *   LDU_ERR_UNSUPPORTED before any GPU work.  At most 262144 stored
+ *   off-diagonal slots (8 per row on average, padding included): this limit
+ *   is checked on the device after the addressing has been validated (the
+ *   stream is synchronised for it), and an input beyond it also returns
+ *   LDU_ERR_UNSUPPORTED, before the matrix is repacked.
  *   owner, neighbour, diag, upper, lower, b: device arrays as in ldu_create
  *   and pcg_solve; x: device double[n], initial guess in, solution out;
  *   iters, relres: host, may be NULL.

@@ -7,8 +7,11 @@ the CUDA path; the two meet only in the seeded inputs of `ldu_cases`.
 Routines (C source in ldu_oracle.c, each citing what it restates):
   spmv, pcg, pipecg, mixed_pipecg, face_grad, value_grad, harmonic_coeffs, harmonic_grad,
   lu_solve, true_relres
-plus two plain numpy helpers, `dense` (the LDU matrix written out densely)
-and `matrix_from_coef` (the FVM matrix of a set of face coefficients).
+plus `lanczos_cond` (the condition number estimate of M^-1 A from CG's own
+coefficients), and two plain numpy helpers, `dense` (the LDU matrix written
+out densely) and `matrix_from_coef` (the FVM matrix of a set of face
+coefficients).  `pcg(..., omp=True)` runs the same Jacobi-PCG from the
+OpenMP build of the source on every host core (`threads()` says how many).
 """
 import ctypes
 
@@ -18,16 +21,15 @@ from . import build_oracle
 
 OK, NOT_CONVERGED, BAD_ARG, NOT_SPD, OOM = 0, 1, -1, -3, -6
 
-_lib = None
+_libs = {}
 _d = ctypes.POINTER(ctypes.c_double)
 _i32 = ctypes.POINTER(ctypes.c_int32)
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build_oracle.build())
-        L = _lib
+def lib(omp=False):
+    if omp not in _libs:
+        L = ctypes.CDLL(build_oracle.build(omp=omp))
+        _libs[omp] = L
         i64, c_int, c_double = ctypes.c_int64, ctypes.c_int, ctypes.c_double
         pint = ctypes.POINTER(c_int)
         mat = [i64, i64, _i32, _i32, _d, _d, _d]
@@ -35,13 +37,15 @@ def lib():
         L.or_spmv.restype = None
         L.or_true_relres.argtypes = mat + [_d, _d]
         L.or_true_relres.restype = c_double
-        L.or_pcg.argtypes = mat + [_d, _d, c_double, c_int, c_int, pint, _d, _d]
+        L.or_pcg.argtypes = mat + [_d, _d, c_double, c_int, c_int, pint, _d, _d, _d]
         L.or_pcg.restype = c_int
         L.or_pipecg.argtypes = mat + [_d, _d, c_double, c_int, c_int, pint, _d, _d]
         L.or_pipecg.restype = c_int
         L.or_mixed_pipecg.argtypes = mat + [_d, _d, c_double, c_int, c_double, c_int, c_int,
                                             c_int, pint, pint, _d]
         L.or_mixed_pipecg.restype = c_int
+        L.or_mixed_pipecg_ex.argtypes = L.or_mixed_pipecg.argtypes + [c_int, _d, c_int, pint]
+        L.or_mixed_pipecg_ex.restype = c_int
         L.or_face_grad.argtypes = [i64, _i32, _i32, _d, _d, _d]
         L.or_face_grad.restype = None
         L.or_value_grad.argtypes = [i64, i64, _i32, _i32, _d, _d, _d, _d, _d]
@@ -52,7 +56,14 @@ def lib():
         L.or_harmonic_grad.restype = None
         L.or_lu_solve.argtypes = [i64, _d, _d]
         L.or_lu_solve.restype = c_int
-    return _lib
+        L.or_threads.argtypes = []
+        L.or_threads.restype = c_int
+    return _libs[omp]
+
+
+def threads(omp=False):
+    """Host threads the Jacobi-PCG of that build uses (1 for the plain build)."""
+    return int(lib(omp).or_threads())
 
 
 def _f64(a):
@@ -100,17 +111,76 @@ class Result:
         return f"Result(status={self.status}, iters={self.iters}, relres={self.relres:.3e})"
 
 
-def pcg(s, b=None, x0=None, tol=1e-8, maxit=20000, jacobi=True, history=False):
-    """Jacobi-preconditioned CG (jacobi=False: plain CG)."""
+def pcg(s, b=None, x0=None, tol=1e-8, maxit=20000, jacobi=True, history=False, coeffs=False,
+        omp=False):
+    """Jacobi-preconditioned CG (jacobi=False: plain CG).  coeffs=True also
+    returns CG's alpha_k and beta_k (Result.alpha, Result.beta; beta_k = 0
+    where the search restarted).  omp=True: the OpenMP build (all host cores)."""
     args, keep = _mat(s)
     b = _f64(s.b if b is None else b)
     x = np.zeros(s.n) if x0 is None else _f64(x0).copy()
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
     hist = np.full(maxit + 1, np.nan) if history else None
-    st = lib().or_pcg(*args, _p(b), _p(x), tol, maxit, int(bool(jacobi)), ctypes.byref(it),
-                      ctypes.byref(rr), _p(hist) if history else None)
-    return Result(x, st, it.value, rr.value, hist)
+    ab = np.zeros(2 * max(maxit, 1)) if coeffs else None
+    st = lib(omp).or_pcg(*args, _p(b), _p(x), tol, maxit, int(bool(jacobi)), ctypes.byref(it),
+                         ctypes.byref(rr), _p(hist) if history else None,
+                         _p(ab) if coeffs else None)
+    kw = {}
+    if coeffs:
+        kw = dict(alpha=ab[0:2 * it.value:2].copy(), beta=ab[1:2 * it.value:2].copy())
+    return Result(x, st, it.value, rr.value, hist, **kw)
+
+
+def lanczos_cond(s, b=None, tol=1e-10, maxit=20000, jacobi=True, omp=False):
+    """(kappa, lambda_min, lambda_max): extreme eigenvalue estimates of M^-1 A
+    (M = diag(A); jacobi=False: of A) from the Lanczos tridiagonal matrix that
+    CG builds implicitly (Saad, Iterative Methods, Sec. 6.7.3); see
+    cond_from_coeffs."""
+    r = pcg(s, b=b, tol=tol, maxit=maxit, jacobi=jacobi, coeffs=True, omp=omp)
+    return cond_from_coeffs(r.alpha, r.beta)
+
+
+def cond_from_coeffs(alpha, beta):
+    """(kappa, lambda_min, lambda_max) from CG's alpha_k and beta_k: the
+    Lanczos tridiagonal matrix
+        T[k, k]     = 1/alpha_k + beta_(k-1)/alpha_(k-1)   (beta_(-1) = 0)
+        T[k, k + 1] = sqrt(beta_k) / alpha_k
+    has Ritz values that approach the extreme eigenvalues of M^-1 A from
+    inside as CG proceeds.  Only the steps before the first restart
+    (beta_k = 0) are used: a restart begins a new Lanczos sequence."""
+    from scipy.linalg import eigh_tridiagonal
+    a, bt = np.asarray(alpha, float), np.asarray(beta, float)
+    k = len(a)
+    cut = np.flatnonzero(bt[:k - 1] == 0.0)
+    if cut.size:
+        k = int(cut[0]) + 1
+    a, bt = a[:k], bt[:k]
+    diag = 1.0 / a
+    diag[1:] += bt[:k - 1] / a[:k - 1]
+    off = np.sqrt(bt[:k - 1]) / a[:k - 1]
+    ev = eigh_tridiagonal(diag, off, eigvals_only=True)
+    return float(ev[-1] / ev[0]), float(ev[0]), float(ev[-1])
+
+
+def reference_solution(s, b=None, tol=4e-15, maxit=None, omp=True):
+    """The tight FP64 reference x* = A^-1 b: Jacobi-PCG run to relative
+    residual `tol` (4e-15: about where FP64 rounding of b - A x stops the
+    true residual on these meshes, near 1e-15) or until it stagnates at the
+    iteration cap.  Returns (x*, its true relres, kappa estimate of M^-1 A
+    from the same run's Lanczos coefficients)."""
+    maxit = maxit or max(20 * int(round(s.n ** (1.0 / 3.0))) + 200, 400)
+    r = pcg(s, b=b, tol=tol, maxit=maxit, coeffs=True, omp=omp)
+    if r.status not in (OK, NOT_CONVERGED):
+        raise RuntimeError(f"reference solve failed: {r}")
+    return r.x, r.relres, cond_from_coeffs(r.alpha, r.beta)[0]
+
+
+def accuracy_tol(kappa, target=1e-8, floor=1e-13):
+    """Residual tolerance whose solutions have relative error <= target:
+    ||x - x*|| / ||x*|| <= kappa ||b - A x|| / ||b||, so target / kappa,
+    floored at 1e-13 (below it FP64 rounding of b - A x decides)."""
+    return max(target / kappa, floor)
 
 
 def pipecg(s, b=None, x0=None, tol=1e-8, maxit=20000, rr_period=0, history=False):
@@ -127,20 +197,37 @@ def pipecg(s, b=None, x0=None, tol=1e-8, maxit=20000, rr_period=0, history=False
 
 
 def mixed_pipecg(s, b=None, x0=None, tol=1e-8, period=12, tau=0.0, restart=False,
-                 maxit=20000, deflate=False):
+                 maxit=20000, deflate=False, sigma1=False, trace=False):
     """FP32 pipelined Jacobi-PCG with FP64 residual replacement every `period`
     iterations (and when gamma dropped by tau^2, or convergence is predicted);
-    restart=True turns the replacements into classic defect-correction restarts."""
+    restart=True turns the replacements into classic defect-correction restarts.
+    sigma1=True keeps the float unit at 1 (no power-of-two rescaling).
+    trace=True also returns Result.trace, one row per event (see TRACE_*)."""
     args, keep = _mat(s)
     b = _f64(s.b if b is None else b)
     x = np.zeros(s.n) if x0 is None else _f64(x0).copy()
     it = ctypes.c_int(0)
     nrep = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
-    st = lib().or_mixed_pipecg(*args, _p(b), _p(x), tol, period, tau, int(bool(restart)),
-                               int(bool(deflate)), maxit,
-                               ctypes.byref(it), ctypes.byref(nrep), ctypes.byref(rr))
-    return Result(x, st, it.value, rr.value, replacements=nrep.value)
+    cap = 3 * maxit + 8 if trace else 0
+    tr = np.zeros((cap, 6)) if trace else None
+    ntr = ctypes.c_int(0)
+    st = lib().or_mixed_pipecg_ex(*args, _p(b), _p(x), tol, period, tau, int(bool(restart)),
+                                  int(bool(deflate)), maxit,
+                                  ctypes.byref(it), ctypes.byref(nrep), ctypes.byref(rr),
+                                  1 if sigma1 else 0, _p(tr) if trace else None, cap,
+                                  ctypes.byref(ntr))
+    kw = {"replacements": nrep.value}
+    if trace:
+        kw["trace"] = tr[:ntr.value].copy()
+    return Result(x, st, it.value, rr.value, **kw)
+
+
+# columns of mixed_pipecg's trace rows
+TRACE_IT, TRACE_EVENT = 0, 1
+TRACE_STEP_AP, TRACE_STEP_GRATIO, TRACE_STEP_DENOM = 2, 3, 4
+TRACE_REP_PREDICTED, TRACE_REP_RELRES, TRACE_REP_WR, TRACE_REP_TRIGGER = 2, 3, 4, 5
+TRIG_FORCED, TRIG_PERIOD, TRIG_TAU, TRIG_PREDICTED, TRIG_CAP = 1, 2, 4, 8, 16
 
 
 def face_grad(owner, neighbour, lam, x):

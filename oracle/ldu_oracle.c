@@ -28,11 +28,23 @@
  * at exit; iters counts the products A*(search direction) of the loop.
  * Status: 0 converged, 1 not converged within the iteration cap,
  * -1 bad argument, -3 breakdown (the matrix is not SPD), -6 out of memory.
+ *
+ * Two builds of this one source: the plain single-threaded one (the oracle
+ * the tests pin and compare against) and, compiled with -fopenmp, a build
+ * whose Jacobi-PCG (or_pcg only) spreads its cell loops over the host cores:
+ * the face loop of the product becomes a loop over cells, each row summing
+ * the faces that touch it in increasing face order, which is the order in
+ * which the face loop adds them, so both builds form bitwise the same A x;
+ * only the dot products' summation order differs.  The OpenMP build serves
+ * the benchmark's multi-core CPU baseline and its tight reference solutions.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_OK 0
 #define OR_NOT_CONVERGED 1
@@ -95,83 +107,225 @@ double or_true_relres(int64_t n, int64_t nf, const int32_t *own, const int32_t *
     return bn > 0.0 ? rn / bn : rn;
 }
 
+/* ---- the operator of one Jacobi-PCG solve ----------------------------------
+ * Plain build: A x is or_spmv's face loop, dots and updates are plain loops.
+ * OpenMP build: rows are formed independently from the list of faces that
+ * touch each cell (built once per solve, faces in increasing order, so each
+ * row adds its face terms in the face loop's order) and every cell loop is
+ * shared among the threads; dot products are OpenMP sum reductions. */
+typedef struct {
+    int64_t n, nf;
+    const int32_t *own, *nbr;
+    const double *diag, *upper, *lower;
+#ifdef _OPENMP
+    int64_t *rstart;   /* [n + 1]: faces of cell i are rface[rstart[i] .. rstart[i+1]) */
+    int64_t *rface;    /* [2 nf]: 2 f + 1 where the cell is the face's neighbour (lower) */
+#endif
+} pcg_op;
+
+static int op_init(pcg_op *A, int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
+                   const double *diag, const double *upper, const double *lower)
+{
+    A->n = n; A->nf = nf; A->own = own; A->nbr = nbr;
+    A->diag = diag; A->upper = upper; A->lower = lower;
+#ifdef _OPENMP
+    A->rstart = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    A->rface = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * nf > 0 ? 2 * nf : 1));
+    if (!A->rstart || !A->rface) {
+        free(A->rstart); free(A->rface);
+        return OR_OOM;
+    }
+    for (int64_t f = 0; f < nf; f++) {
+        A->rstart[own[f] + 1]++;
+        A->rstart[nbr[f] + 1]++;
+    }
+    for (int64_t i = 0; i < n; i++)
+        A->rstart[i + 1] += A->rstart[i];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!fill) {
+        free(A->rstart); free(A->rface);
+        return OR_OOM;
+    }
+    for (int64_t i = 0; i < n; i++)
+        fill[i] = A->rstart[i];
+    for (int64_t f = 0; f < nf; f++) {
+        A->rface[fill[own[f]]++] = 2 * f;
+        A->rface[fill[nbr[f]]++] = 2 * f + 1;
+    }
+    free(fill);
+#endif
+    return OR_OK;
+}
+
+static void op_free(pcg_op *A)
+{
+#ifdef _OPENMP
+    free(A->rstart);
+    free(A->rface);
+#else
+    (void)A;
+#endif
+}
+
+static void op_spmv(const pcg_op *A, const double *x, double *y)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < A->n; i++) {
+        double s = A->diag[i] * x[i];
+        for (int64_t e = A->rstart[i]; e < A->rstart[i + 1]; e++) {
+            int64_t f = A->rface[e] >> 1;
+            if (A->rface[e] & 1)
+                s += A->lower[f] * x[A->own[f]];
+            else
+                s += A->upper[f] * x[A->nbr[f]];
+        }
+        y[i] = s;
+    }
+#else
+    or_spmv(A->n, A->nf, A->own, A->nbr, A->diag, A->upper, A->lower, x, y);
+#endif
+}
+
+static double op_dot(const pcg_op *A, const double *a, const double *b)
+{
+    double s = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) reduction(+ : s)
+#endif
+    for (int64_t i = 0; i < A->n; i++)
+        s += a[i] * b[i];
+    return s;
+}
+
+/* r = b - A x */
+static void op_residual(const pcg_op *A, const double *b, const double *x, double *r)
+{
+    op_spmv(A, x, r);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < A->n; i++)
+        r[i] = b[i] - r[i];
+}
+
+/* z = M^-1 r with M = diag(A) (Jacobi), or z = r without a preconditioner;
+ * then p = z when p is given */
+static void op_precond(const pcg_op *A, int use_jacobi, const double *r, double *z, double *p)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int64_t i = 0; i < A->n; i++) {
+        z[i] = use_jacobi ? r[i] / A->diag[i] : r[i];
+        if (p)
+            p[i] = z[i];
+    }
+}
+
+/* Number of threads the solves of this build use (1 for the plain build). */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 /* ---- Jacobi-preconditioned CG (Saad, Iterative Methods, Alg. 9.1) ---------
  * Stops when the recursively updated ||r||/||b|| reaches tol; the residual
  * is then recomputed as b - A x, and if that true residual is still above
  * tol it replaces r and the search restarts from p = M^-1 r.
- * hist (optional, maxit+1 entries) receives the recursive relres per step. */
+ * hist (optional, maxit+1 entries) receives the recursive relres per step.
+ * ab (optional, 2 maxit entries) receives alpha_k and beta_k of every step k
+ * (beta_k = 0 where the search restarted): the coefficients of the Lanczos
+ * tridiagonal matrix of M^-1 A that CG builds implicitly (Saad, Sec. 6.7.3). */
 int or_pcg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
            const double *diag, const double *upper, const double *lower,
            const double *b, double *x, double tol, int maxit, int use_jacobi,
-           int *iters, double *relres, double *hist)
+           int *iters, double *relres, double *hist, double *ab)
 {
     if (n < 0 || nf < 0 || maxit < 0 || !(tol >= 0.0))
         return OR_BAD_ARG;
     *iters = 0;
-    double bnorm = sqrt(dot(n, b, b));
+    pcg_op A;
+    if (op_init(&A, n, nf, own, nbr, diag, upper, lower) != OR_OK)
+        return OR_OOM;
+    double bnorm = sqrt(op_dot(&A, b, b));
     if (bnorm == 0.0) {
         for (int64_t i = 0; i < n; i++)
             x[i] = 0.0;
         *relres = 0.0;
+        op_free(&A);
         return OR_OK;
     }
-    size_t bytes = sizeof(double) * (size_t)n;
+    size_t bytes = sizeof(double) * (size_t)(n > 0 ? n : 1);
     double *r = (double *)malloc(bytes), *z = (double *)malloc(bytes);
     double *p = (double *)malloc(bytes), *q = (double *)malloc(bytes);
     if (!r || !z || !p || !q) {
         free(r); free(z); free(p); free(q);
+        op_free(&A);
         return OR_OOM;
     }
     int status = OR_NOT_CONVERGED, it = 0;
-    residual(n, nf, own, nbr, diag, upper, lower, b, x, r);
-    double rnorm = sqrt(dot(n, r, r));
+    op_residual(&A, b, x, r);
+    double rnorm = sqrt(op_dot(&A, r, r));
     if (hist)
         hist[0] = rnorm / bnorm;
     if (rnorm / bnorm <= tol) {
         status = OR_OK;
         goto done;
     }
-    precond(n, use_jacobi, diag, r, z);
-    for (int64_t i = 0; i < n; i++)
-        p[i] = z[i];
-    double rz = dot(n, r, z);
+    op_precond(&A, use_jacobi, r, z, p);
+    double rz = op_dot(&A, r, z);
     for (;;) {
         if (it >= maxit) {
             status = OR_NOT_CONVERGED;
             break;
         }
-        or_spmv(n, nf, own, nbr, diag, upper, lower, p, q);
-        double pq = dot(n, p, q);
+        op_spmv(&A, p, q);
+        double pq = op_dot(&A, p, q);
         if (!(pq > 0.0)) {
             status = OR_NOT_SPD;
             break;
         }
         double alpha = rz / pq;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (int64_t i = 0; i < n; i++) {
             x[i] += alpha * p[i];
             r[i] -= alpha * q[i];
         }
+        if (ab) {
+            ab[2 * it] = alpha;
+            ab[2 * it + 1] = 0.0;
+        }
         it++;
-        rnorm = sqrt(dot(n, r, r));
+        rnorm = sqrt(op_dot(&A, r, r));
         if (hist)
             hist[it] = rnorm / bnorm;
         if (rnorm / bnorm <= tol) {
-            residual(n, nf, own, nbr, diag, upper, lower, b, x, r);
-            rnorm = sqrt(dot(n, r, r));
+            op_residual(&A, b, x, r);
+            rnorm = sqrt(op_dot(&A, r, r));
             if (rnorm / bnorm <= tol) {
                 status = OR_OK;
                 break;
             }
-            precond(n, use_jacobi, diag, r, z);
-            for (int64_t i = 0; i < n; i++)
-                p[i] = z[i];
-            rz = dot(n, r, z);
+            op_precond(&A, use_jacobi, r, z, p);
+            rz = op_dot(&A, r, z);
             continue;
         }
-        precond(n, use_jacobi, diag, r, z);
-        double rz_new = dot(n, r, z);
+        op_precond(&A, use_jacobi, r, z, NULL);
+        double rz_new = op_dot(&A, r, z);
         double beta = rz_new / rz;
         rz = rz_new;
+        if (ab)
+            ab[2 * it - 1] = beta;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (int64_t i = 0; i < n; i++)
             p[i] = z[i] + beta * p[i];
     }
@@ -179,6 +333,7 @@ done:
     *iters = it;
     *relres = or_true_relres(n, nf, own, nbr, diag, upper, lower, b, x);
     free(r); free(z); free(p); free(q);
+    op_free(&A);
     return status;
 }
 
@@ -378,12 +533,34 @@ static double dot32(int64_t n, const float *a, const float *b)
  * float iteration, where the rounding of the float operator cannot resolve
  * it.  W, a1, M^-1 a1 and A M^-1 a1 are formed in FP64 and rounded to
  * float for the recurrences. */
-int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
-                    const double *diag, const double *upper, const double *lower,
-                    const double *b, double *x, double tol, int period, double tau,
-                    int restart, int deflate, int maxit, int *iters, int *replacements,
-                    double *relres)
+/* Trace of or_mixed_pipecg_ex (for the tests that pin its control logic):
+ * one record of OR_TRACE_LEN doubles per event,
+ *   [0] iteration count at the event, [1] event: 0 step, 1 replacement,
+ *   step:        [2] (a1, p)/(|a1| |p|) after the update (deflation; else 0),
+ *                [3] gamma / gamma_ref of the fresh dot products,
+ *                [4] the denominator alpha was formed with, divided by
+ *                    (p, A p) of the new direction (FP64 matrix; equal in
+ *                    exact arithmetic),
+ *   replacement: [2] the predicted relres sqrt(ratio gamma) sigma/||b|| that
+ *                    the trigger saw, [3] the true relres after the fold (and
+ *                    coarse correction), [4] (W, r64)/(|W| |r64|) after the
+ *                    coarse correction (deflation; else 0),
+ *                [5] trigger bits: 1 forced (start or breakdown), 2 period,
+ *                    4 tau drop, 8 predicted convergence, 16 iteration cap.
+ * flags: OR_MIXED_SIGMA1 keeps the float unit sigma at 1 instead of the power
+ * of two nearest sqrt(r64, M^-1 r64). */
+#define OR_TRACE_LEN 6
+#define OR_MIXED_SIGMA1 1
+
+int or_mixed_pipecg_ex(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
+                       const double *diag, const double *upper, const double *lower,
+                       const double *b, double *x, double tol, int period, double tau,
+                       int restart, int deflate, int maxit, int *iters, int *replacements,
+                       double *relres, int flags, double *trace, int trace_cap, int *trace_len)
 {
+    int ntr = 0;
+    if (trace_len)
+        *trace_len = 0;
     if (n < 0 || nf < 0 || maxit < 0 || period < 0 || !(tol >= 0.0) || !(tau >= 0.0))
         return OR_BAD_ARG;
     *iters = 0;
@@ -451,9 +628,9 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
         double delta = dot32(n, w, u);
         double eps = deflate ? dot32(n, a132, u) : 0.0;
         double predicted = sqrt(ratio * gamma) * sigma / bnorm;
-        int trigger = force || (period > 0 && since >= period)
-                      || (tau > 0.0 && gamma <= tau * tau * gamma_ref)
-                      || predicted <= tol || it >= maxit;
+        int trigger = (force ? 1 : 0) | ((period > 0 && since >= period) ? 2 : 0)
+                      | ((tau > 0.0 && gamma <= tau * tau * gamma_ref) ? 4 : 0)
+                      | (predicted <= tol ? 8 : 0) | (it >= maxit ? 16 : 0);
         if (trigger) {
             for (int64_t i = 0; i < n; i++) {
                 x[i] += sigma * (double)xc[i];
@@ -473,6 +650,17 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
             nrep++;
             double rn2 = dot(n, r64, r64);
             *relres = sqrt(rn2) / bnorm;
+            if (trace && ntr < trace_cap) {
+                double *t = trace + (size_t)OR_TRACE_LEN * ntr++;
+                double wr = 0.0;
+                if (deflate) {
+                    for (int64_t i = 0; i < n; i++)
+                        wr += r64[i];                       /* (W, r64), W = 1 */
+                    wr /= sqrt((double)n) * sqrt(rn2) + 1e-300;
+                }
+                t[0] = it; t[1] = 1; t[2] = predicted; t[3] = *relres; t[4] = wr;
+                t[5] = trigger;
+            }
             if (*relres <= tol) {
                 status = OR_OK;
                 break;
@@ -489,7 +677,7 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
                 break;
             }
             ratio = rn2 / g64;
-            double sigma_new = exp2(round(log2(sqrt(g64))));
+            double sigma_new = (flags & OR_MIXED_SIGMA1) ? 1.0 : exp2(round(log2(sqrt(g64))));
             if (restart) {
                 for (int64_t i = 0; i < n; i++)
                     p[i] = 0.0f;
@@ -558,6 +746,25 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
             u[i] -= a * q[i];
             w[i] -= a * z[i];
         }
+        if (trace && ntr < trace_cap) {
+            double *t = trace + (size_t)OR_TRACE_LEN * ntr++;
+            double ap = 0.0, aa = 0.0, pp = 0.0, pap = 0.0;
+            if (deflate) {
+                for (int64_t i = 0; i < n; i++) {
+                    ap += a1[i] * (double)p[i];
+                    aa += a1[i] * a1[i];
+                    pp += (double)p[i] * (double)p[i];
+                }
+                ap /= sqrt(aa) * sqrt(pp) + 1e-300;
+            }
+            for (int64_t i = 0; i < n; i++)
+                t64[i] = (double)p[i];
+            or_spmv(n, nf, own, nbr, diag, upper, lower, t64, r64);
+            for (int64_t i = 0; i < n; i++)
+                pap += t64[i] * r64[i];
+            t[0] = it + 1; t[1] = 0; t[2] = ap; t[3] = gamma_ref > 0.0 ? gamma / gamma_ref : 0.0;
+            t[4] = denom / pap; t[5] = 0.0;
+        }
         gamma_old = gamma;
         alpha_old = alpha;
         it++;
@@ -565,11 +772,24 @@ int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nb
     }
     *iters = it;
     *replacements = nrep;
+    if (trace_len)
+        *trace_len = ntr;
 out:
     free(r64); free(a1); free(t64); free(d32); free(u32); free(l32);
     for (int k = 0; k < 14; k++)
         free(v[k]);
     return status;
+}
+
+int or_mixed_pipecg(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
+                    const double *diag, const double *upper, const double *lower,
+                    const double *b, double *x, double tol, int period, double tau,
+                    int restart, int deflate, int maxit, int *iters, int *replacements,
+                    double *relres)
+{
+    return or_mixed_pipecg_ex(n, nf, own, nbr, diag, upper, lower, b, x, tol, period, tau,
+                              restart, deflate, maxit, iters, replacements, relres, 0, NULL, 0,
+                              NULL);
 }
 
 /* ---- adjoint face gradient ------------------------------------------------

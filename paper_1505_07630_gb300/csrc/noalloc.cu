@@ -14,7 +14,10 @@
 // The scratch is shared by all calls on a device and keeps whatever the last
 // call left in it; everything a call relies on starting at zero is cleared
 // by that call.  Calls whose work overlaps on the GPU (two streams, two
-// host threads) race on the scratch.
+// host threads) race on the scratch.  The scratch's device address is looked
+// up once per device, by the first call on it, and kept for the life of the
+// process: after a cudaDeviceReset (which unloads the module and frees the
+// array) this entry point must not be called again in the same process.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -167,6 +170,9 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
     CK(cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)n, st));
     CK(cudaMemsetAsync(cursor, 0, sizeof(int) * (size_t)n, st));
     CK(cudaMemsetAsync(words, 0, kWordsBytes, st));
+    // the result block reads as "no result" (status -1) until the kernel
+    // writes it, so a launch that ends without writing it is an error
+    CK(cudaMemsetAsync(out, 0xff, sizeof(SolveOut), st));
 
     if (nFaces > 0)
         k_validate_count<<<noalloc_blocks(nFaces, 256), 256, 0, st>>>(nFaces, (int)n, owner,
