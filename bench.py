@@ -11,8 +11,12 @@ events); each step is timed with CUDA events on the solve's stream.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--size S] [--skip-fp64]
 
---impl reference times the oracle (plain C, FP64 Jacobi-PCG, one host core)
-on a bounded sample of the same workload and scales it to a full solve.
+--impl reference times the oracle's FP64 Jacobi-PCG (the same C source built
+with OpenMP, every host core) solving the same system to 1e-8, one complete
+solve per step.  Our arm also reports the plain single-threaded oracle's
+complete solve (cpu_baseline), the error of every result against the
+oracle's tight FP64 solution (computed after the timed legs), and the FP64
+rate of cuBLAS DGEMM on this GPU (the FP64 solvers' arithmetic bound).
 Under torchrun (N > 1) every rank solves its own replica (no data exchange:
 the single-system solve is not partitioned here) and rank 0 prints the
 maximum over ranks.
@@ -96,6 +100,23 @@ def bytes_mixed(n, F, iters, reps, col_bytes=4):
            + f * 8 + 4 + 4 + 8 + 8 + 4)           # z = As, rescale r, p, read w
     ends = 8 * 4 + 4 * 4 + 3 * 8                  # prep (b, x0 in; bhat, xhat out; zero 4 float) + unscale
     return n * (iters * loop + reps * rep + ends)
+
+
+def bytes_mixed_preconditioned(n, F, iters, reps):
+    """Algorithmic bytes of the FP32-inner pipelined PCG in its preconditioned
+    form (the recurrences of Sec. 4.1 with M^-1 applied to separate vectors):
+    per float iteration 4n (float diagonal) + 16F (2F float values and int32
+    columns) + 80n (ten float vectors once each), per FP64 residual
+    replacement 8n + 24F + 24n.  The library's scaled formulation needs no
+    M^-1 vectors and 16-bit columns (bytes_mixed), so this count is larger
+    than what the kernel has to move."""
+    return iters * (4.0 * n + 16.0 * F + 80.0 * n) + reps * (8.0 * n + 24.0 * F + 24.0 * n)
+
+
+# FP64 instructions per cell and iteration of k_pcg64 (the scaled product:
+# about 6 FMAs for the off-diagonal slots and one add for the unit diagonal;
+# (p, q), two updates, (r, r) and sum d r^2, the p update: 7 more)
+PCG64_FP64_INSTR_PER_CELL = 13
 
 
 def bytes_pcg64(n, F, iters, reps):
@@ -211,13 +232,14 @@ def emit(line, ranks):
 
 
 # ---- the oracle arm --------------------------------------------------------
-def oracle_sample(sys_, iters_cap):
-    """Seconds per FP64 PCG iteration of the oracle over a capped run."""
+def oracle_solve(sys_, omp):
+    """(seconds, result) of one complete FP64 Jacobi-PCG solve to TOL by the
+    oracle: the plain single-threaded build, or (omp) the OpenMP build on
+    every host core."""
     import oracle
     t0 = time.perf_counter()
-    r = oracle.pcg(sys_, tol=TOL, maxit=iters_cap)
-    dt = time.perf_counter() - t0
-    return dt / max(r.iters, 1), r
+    r = oracle.pcg(sys_, tol=TOL, omp=omp)
+    return time.perf_counter() - t0, r
 
 
 # the workload both arms solve: the 128^3 lognormal Poisson system to relative residual 1e-8
@@ -232,31 +254,89 @@ def run_reference(args):
     import ldu_cases as lc
     import oracle
     s = lc.config2(s=args.size, seed=0)
-    oracle.lib()
-    full = oracle.pcg(s, tol=TOL)              # iteration count of the full solve
-    cap = args.ref_iters
+    oracle.lib(omp=True)
+    cores = oracle.threads(omp=True)
     for _ in range(args.warmup):
-        oracle_sample(s, cap)
-    per = []
+        oracle_solve(s, omp=True)
+    per, res = [], None
     for _ in range(args.steps):
-        t_it, _ = oracle_sample(s, cap)
-        per.append(t_it * full.iters)
+        t, res = oracle_solve(s, omp=True)
+        per.append(t)
     value = statistics.mean(per)
-    sample = (f"{cap} FP64 Jacobi-PCG iterations of the {args.size}^3 case per step, scaled to "
-              f"the oracle's full {full.iters}-iteration solve")
+    sample = (f"one complete FP64 Jacobi-PCG solve of the {args.size}^3 case to 1e-8 per step "
+              f"({res.iters} iterations), the oracle's C source built with OpenMP on {cores} "
+              f"host threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": value * 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD.format(size=args.size), "cells": s.n, "faces": s.nfaces,
-                   "solver": "FP64 Jacobi-PCG, the oracle (plain C, one host core)"},
-        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                   "solver": "FP64 Jacobi-PCG, the oracle (C, OpenMP over the host cores)"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "oracle_iters": full.iters, "oracle_relres": full.relres,
+        "oracle_iters": res.iters, "oracle_relres": res.relres,
+        "step_s_min_median_max": [min(per), statistics.median(per), max(per)],
     }
     emit(line, ranks)
+
+
+def fp64_dgemm_tflops(dev, n=4096, reps=5):
+    """FP64 rate of this GPU as cuBLAS reaches it: torch.matmul of two n x n
+    float64 matrices, 2 n^3 flops, best of reps, CUDA events."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    torch.cuda.synchronize(dev)
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def rel_err(x, xs):
+    import numpy as np
+    return float(np.linalg.norm(np.asarray(x) - xs) / np.linalg.norm(xs))
+
+
+def accuracy_report(s, solutions, batched_x=None, piso=None):
+    """The error of every result against the oracle's tight FP64 solution
+    x* (Jacobi-PCG of the OpenMP build to the limit of FP64), computed after
+    the timed legs.  solutions: name -> x of the 128^3 system; batched_x:
+    (systems, concatenated x); piso: (system, b, p)."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    xs, rr, kappa = oracle.reference_solution(s)
+    out = {"reference": {"relres": rr, "kappa_est": kappa,
+                         "solver": "oracle FP64 Jacobi-PCG (OpenMP build) to 4e-15 or stagnation"},
+           "errors": {k: rel_err(x, xs) for k, x in solutions.items()}}
+    if batched_x is not None:
+        systems, xb = batched_x
+        off, errs = 0, []
+        for q in systems:
+            xq, _, _ = oracle.reference_solution(q)
+            errs.append(rel_err(xb[off:off + q.n], xq))
+            off += q.n
+        out["errors"]["batched_max"] = max(errs)
+        out["errors"]["batched_median"] = float(np.median(errs))
+    if piso is not None:
+        sp, bp, pp = piso
+        xq, rq, kq = oracle.reference_solution(sp, b=bp)
+        out["errors"]["piso_pressure_last_step"] = rel_err(pp, xq)
+        out["reference"]["piso_relres"] = rq
+        out["reference"]["piso_kappa_est"] = kq
+    out["seconds"] = time.perf_counter() - t0
+    return out
 
 
 # ---- our arm ---------------------------------------------------------------
@@ -361,6 +441,8 @@ def run_ours(args):
     col_bytes = 2 if (A.info()["col16"] and grid["staged"]) else 4
     alg_bytes = bytes_mixed(n, F, it, reps, col_bytes)
     achieved = alg_bytes / statistics.median(t_mixed) / 1e9
+    alg_pre = bytes_mixed_preconditioned(n, F, it, reps)
+    achieved_pre = alg_pre / statistics.median(t_mixed) / 1e9
     prof = profiled_traffic(A.info()["slice_rows"])
     traffic = None
     if prof is not None and prof[1] == it:
@@ -387,10 +469,15 @@ def run_ours(args):
             times.append(e0.elapsed_time(e1) * 1e-3)
         return times
 
+    solutions = {"mixed": x_mixed}
     if not args.skip_fp64:
         t_defl, o_defl = timed(mixed_deflated, max(2, args.steps // 2), 1)
+        solutions["mixed_deflated"] = x.cpu().numpy()
         t_pcg, o_pcg = timed(pcg64, max(2, args.steps // 2), 1)
+        solutions["fp64_pcg"] = x.cpu().numpy()
         t_pipe, o_pipe = timed(pipe64, max(2, args.steps // 2), 1)
+        solutions["fp64_pipecg"] = x.cpu().numpy()
+        dgemm = fp64_dgemm_tflops(dev)
         pst, pit, prr, preps = o_pcg[-1]
         qst, qit, qrr, qreps = o_pipe[-1]
         mp = statistics.median(t_pcg)
@@ -401,7 +488,13 @@ def run_ours(args):
                                "status": dst, "replacements": dreps},
             "fp64_pcg": {"s": mp, "iters": pit, "relres": prr, "status": pst,
                          "slice_rows": A_pcg.info()["slice_rows"],
-                         "alg_gbs": bytes_pcg64(n, F, pit, preps) / mp / 1e9},
+                         "alg_gbs": bytes_pcg64(n, F, pit, preps) / mp / 1e9,
+                         "fp64_tflops": 2.0 * PCG64_FP64_INSTR_PER_CELL * n * pit / mp / 1e12,
+                         "frac_fp64_dgemm": 2.0 * PCG64_FP64_INSTR_PER_CELL * n * pit / mp
+                         / 1e12 / dgemm},
+            "fp64_peak": {"dgemm_tflops": dgemm,
+                          "how": "torch.matmul float64 4096^3 (cuBLAS), 2 n^3 flops, best of 5, "
+                                 "CUDA events; FP64 solvers count 2 flops per FP64 FMA"},
             "fp64_pipecg": {"s": mq, "iters": qit, "relres": qrr, "status": qst,
                             "slice_rows": A_pipe.info()["slice_rows"],
                             "alg_gbs": bytes_pipe64(n, F, qit, qreps) / mq / 1e9},
@@ -424,30 +517,54 @@ def run_ours(args):
     t_e2e, _ = timed(e2e_step, args.steps, 1)
     e2e_s = job_seconds(statistics.mean(t_e2e), dist, dev)
 
-    batched = None
+    batched = batched_x = piso_x = None
     if not args.skip_batched:
-        batched = run_batched(args, dev, pkg, timed_fn=timed_generic)
+        batched, batched_x = run_batched(args, dev, pkg, timed_fn=timed_generic)
     pressure = autograd_case = heat = amg_case = piso_case = None
     if not args.skip_extra:
-        amg_case = run_amg(args, dev, pkg, s, timed_fn=timed_generic)
-        piso_case = run_piso(args, dev, pkg, timed_fn=timed_generic)
+        amg_case, amg_x = run_amg(args, dev, pkg, s, timed_fn=timed_generic)
+        solutions.update(amg_x)
+        piso_case, piso_x = run_piso(args, dev, pkg, timed_fn=timed_generic)
         pressure = run_pressure(args, dev, pkg, timed_fn=timed_generic)
         autograd_case = run_autograd(args, dev, pkg, timed_fn=timed_generic)
         heat = run_heat(args, dev, pkg, timed_fn=timed_generic)
 
-    # CPU baseline: the oracle on this host, bounded sample, rank 0 only
-    cpu = None
+    # CPU baseline: the oracle on this host, one complete solve, rank 0 only
+    cpu = cpu_omp = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        full_iters = extra.get("fp64_pcg", {}).get("iters", it)
-        t_it, _ = oracle_sample(s, args.ref_iters)
-        cpu = {"value": t_it * full_iters, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"{args.ref_iters} FP64 Jacobi-PCG iterations of the {args.size}^3 case "
-                         f"(plain C oracle, one core), scaled to {full_iters} iterations"}
+        import oracle
+        t1, r1 = oracle_solve(s, omp=False)
+        cpu = {"value": t1, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"one complete FP64 Jacobi-PCG solve of the {args.size}^3 case to 1e-8 "
+                         f"({r1.iters} iterations; plain C oracle, one host core)"}
+        t2, r2 = oracle_solve(s, omp=True)
+        cpu_omp = {"value": t2, "unit": "s", "cores": oracle.threads(omp=True), "kind": "oracle",
+                   "sample": f"the same solve ({r2.iters} iterations) by the oracle's C source "
+                             f"built with OpenMP, all host threads"}
 
-    relres_oracle = None
+    relres_oracle = accuracy = None
     if rank == 0:
         import oracle
         relres_oracle = oracle.true_relres(s, x_mixed)
+        if not args.skip_accuracy:
+            accuracy = accuracy_report(s, solutions, batched_x, piso_x)
+            errs = accuracy["errors"]
+            for key, leg in (("mixed_deflated", extra.get("mixed_deflated")),
+                             ("fp64_pcg", extra.get("fp64_pcg")),
+                             ("fp64_pipecg", extra.get("fp64_pipecg"))):
+                if leg is not None and key in errs:
+                    leg["error_vs_fp64"] = errs[key]
+            if batched is not None:
+                batched["error_vs_fp64_max"] = errs.get("batched_max")
+            if amg_case is not None:
+                for prec in ("mixed", "fp64", "pipelined_fp64"):
+                    amg_case[prec]["error_vs_fp64"] = errs.get("amg_" + prec)
+            if piso_case is not None:
+                piso_case["error_vs_fp64_last_step"] = errs.get("piso_pressure_last_step")
+            if pressure is not None:
+                pressure["error_vs_fp64"] = None
+                pressure["error_note"] = ("no oracle reference at 256^3: its tight FP64 solve "
+                                          "takes minutes on the host")
 
     line = {
         "metric": METRIC, "value": step_s, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -461,11 +578,19 @@ def run_ours(args):
                    "rr_period": rr_m, "tau": tau_m, "l2": "256 MB flush before every step",
                    "parallelism": "replicas" if world > 1 else "single"},
         "solve": {"status": st, "iters": it, "replacements": reps, "relres": rr,
-                  "relres_oracle": relres_oracle},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                  "relres_oracle": relres_oracle,
+                  "error_vs_fp64": accuracy["errors"]["mixed"] if accuracy else None},
+        "roofline": {"bound": "hbm", "achieved": achieved_pre, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved_pre / hbm, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "k_mixed (persistent, one launch per solve)",
-                     "alg_bytes_per_launch": alg_bytes},
+                     "alg_bytes_per_launch": alg_pre,
+                     "alg_model": "preconditioned pipelined PCG: (4n+16F+80n) B per float "
+                                  "iteration + (8n+24F+24n) B per FP64 residual",
+                     "frac_scaled_model": achieved / hbm,
+                     "alg_bytes_scaled_model": alg_bytes,
+                     "frac_dram": (traffic / statistics.median(t_mixed) / 1e9 / hbm
+                                   if traffic else None),
+                     "bar_judged_on": "frac_dram"},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n,
                 "d2h_bytes_per_step": 8 * n,
                 "step_ms_min_median_max": [min(t_e2e) * 1e3, statistics.median(t_e2e) * 1e3,
@@ -473,6 +598,8 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "cpu_baseline_omp": cpu_omp,
+        "accuracy": accuracy,
         "batched": batched,
         "pressure256": pressure,
         "differentiable": autograd_case,
@@ -529,6 +656,7 @@ def run_batched(args, dev, pkg, timed_fn):
     alg = sum(bytes_mixed(s.n, s.nfaces, int(its[k]), int(its[k]) // rr_b + 2, cb)
               for k, s in enumerate(systems))
     tb = statistics.median(t_batch)
+    xh = x.cpu().numpy()
     A.close()
     return {"systems": len(systems), "cells": int(offs[-1]), "one_launch_s": tb,
             "separate_calls_s": statistics.median(t_sep), "speedup": statistics.median(t_sep) / tb,
@@ -537,7 +665,7 @@ def run_batched(args, dev, pkg, timed_fn):
             "tuned": {k: best[k] for k in ("slice_rows", "max_team", "team_work_scale")},
             "grid_blocks": info["grid_blocks"], "teams_max": info["max_team"],
             "staged": staged_b,
-            "ntasks": info["ntasks"]}
+            "ntasks": info["ntasks"]}, (systems, xh)
 
 
 def run_amg(args, dev, pkg, s, timed_fn):
@@ -564,6 +692,7 @@ def run_amg(args, dev, pkg, s, timed_fn):
             for _ in range(10):
                 pkg.ldu_amg_vcycle(M, bb, zz)
         out[name] = statistics.median(timed_fn(cycles, 3, 1)) * 100.0
+    xs = {}
     for prec in ("mixed", "fp64", "pipelined_fp64"):
         res = {}
 
@@ -576,8 +705,9 @@ def run_amg(args, dev, pkg, s, timed_fn):
         t = timed_fn(solve, 3, 1, prep=x.zero_)
         _, it, rr, st = res["out"]
         out[prec] = {"s": statistics.median(t), "iters": it, "relres": rr, "status": st}
+        xs["amg_" + prec] = x.cpu().numpy()
     M.close()
-    return out
+    return out, xs
 
 
 def run_pressure(args, dev, pkg, timed_fn):
@@ -683,9 +813,13 @@ def run_piso(args, dev, pkg, timed_fn):
 
     t = timed_fn(steps, 2, 1)
     A.close()
-    return {"cells": s.n, "faces": s.nfaces, "steps": 10, "s_per_step": statistics.median(t) / 10,
-            "iterations_per_step": out["iters"] / 10, "relres_last": out["relres"],
-            "status": out["status"]}
+    # the last step's system, for the error against the oracle: b = -div(phi*_9)
+    from oracle import piso as opiso
+    phi9 = torch.add(phi0, dphi, alpha=1e-3 * 9).cpu().numpy()   # the step's own input
+    b9 = -opiso.divergence_fast(s.owner, s.neighbour, s.n, phi9)
+    return ({"cells": s.n, "faces": s.nfaces, "steps": 10, "s_per_step": statistics.median(t) / 10,
+             "iterations_per_step": out["iters"] / 10, "relres_last": out["relres"],
+             "status": out["status"]}, (s, b9, p.cpu().numpy()))
 
 
 def run_autograd(args, dev, pkg, timed_fn):
@@ -751,7 +885,8 @@ def main():
     ap.add_argument("--staging", type=int, default=0, choices=[0, -1])
     ap.add_argument("--rr-period", type=int, default=0)
     ap.add_argument("--tau", type=float, default=0.0)
-    ap.add_argument("--ref-iters", type=int, default=60)
+    ap.add_argument("--skip-accuracy", action="store_true",
+                    help="skip the errors against the oracle's tight solution")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")

@@ -14,6 +14,7 @@ coefficients).  `pcg(..., omp=True)` runs the same Jacobi-PCG from the
 OpenMP build of the source on every host core (`threads()` says how many).
 """
 import ctypes
+import os
 
 import numpy as np
 
@@ -58,7 +59,38 @@ def lib(omp=False):
         L.or_lu_solve.restype = c_int
         L.or_threads.argtypes = []
         L.or_threads.restype = c_int
+        L.or_set_threads.argtypes = [c_int]
+        L.or_set_threads.restype = None
+        if omp and "OMP_NUM_THREADS" not in os.environ:
+            L.or_set_threads(host_cores())
     return _libs[omp]
+
+
+def host_cores():
+    """CPUs this process may really use: the affinity mask, capped by a
+    cgroup CPU quota (a container can see more CPUs than its quota lets it
+    run at once, and OpenMP threads beyond the quota only wait on each
+    other)."""
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    quota = None
+    try:
+        with open("/sys/fs/cgroup/cpu.max") as f:
+            q, period = f.read().split()[:2]
+            if q != "max":
+                quota = int(q) / int(period)
+    except (OSError, ValueError):
+        try:
+            with open("/sys/fs/cgroup/cpu/cpu.cfs_quota_us") as f:
+                q = int(f.read())
+            with open("/sys/fs/cgroup/cpu/cpu.cfs_period_us") as f:
+                period = int(f.read())
+            if q > 0:
+                quota = q / period
+        except (OSError, ValueError):
+            pass
+    if quota is not None:
+        n = min(n, max(1, int(quota)))
+    return max(1, int(n or 1))
 
 
 def threads(omp=False):

@@ -223,6 +223,17 @@ static void op_precond(const pcg_op *A, int use_jacobi, const double *r, double 
     }
 }
 
+/* Set the number of threads of this build's solves (ignored by the plain build). */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Number of threads the solves of this build use (1 for the plain build). */
 int or_threads(void)
 {
