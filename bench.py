@@ -670,7 +670,7 @@ def run_batched(args, dev, pkg, timed_fn):
 
 def run_amg(args, dev, pkg, s, timed_fn):
     """Aggregation-AMG preconditioned CG (Sec. 5, Table 2's AMG-CG) on the
-    headline system to 1e-8: hierarchy setup (host, once per matrix), one
+    headline system to 1e-8: hierarchy setup (device kernels, once per matrix), one
     V-cycle in each precision, and the whole solve with the FP64 cycle and
     with the float cycle inside the FP64 outer CG."""
     import time

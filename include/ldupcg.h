@@ -379,14 +379,21 @@ int ldu_piso_pressure(ldu_matrix *A, const double *coef, double *phi, double *p,
  *
  * The paper also preconditions CG with a V-cycle of an aggregation-based
  * algebraic multigrid (aggregates grown around a distance-2 maximal
- * independent set, weighted-Jacobi smoothing).  This library reads it as:
- *   aggregation  rows in increasing order.  Phase 1: a row whose neighbours
- *                (the off-diagonal non-zeros of its row) are all unaggregated
- *                becomes a root and forms an aggregate with them.  Phase 2:
- *                every other unaggregated row joins the phase-1 aggregate of
- *                its strongest neighbour (largest |a_ij|; strengths within a
- *                relative 1e-12 are ties, won by the lower aggregate number).
- *                Phase 3: rows with no aggregated neighbour stand alone;
+ * independent set, weighted-Jacobi smoothing), taken from CUSP, whose
+ * aggregation forms that set in parallel (Bell, Dalton & Olson 2012).  This
+ * library reads it as:
+ *   graph        the stored off-diagonal entries of A (sparsity patterns are
+ *                structural throughout: coarse entries that cancel are kept);
+ *   roots        a distance-2 maximal independent set by Luby-style rounds:
+ *                row i has priority h_i = mix64((i + 1) * 0x9E3779B97F4A7C15)
+ *                (SplitMix64); an undecided row whose (state, h) is the
+ *                largest within two steps becomes a root, one that sees a
+ *                root within two steps is excluded, until every row is
+ *                decided;
+ *   aggregates   roots numbered in row order; a row next to a root joins it;
+ *                every other row joins its assigned neighbour of largest
+ *                |a_ij| (values within 1e-12 of the row's largest |a_ij| are
+ *                ties, won by the lower aggregate number);
  *   prolongator  P = (I - w D^-1 A) P_t with P_t the aggregates' indicator
  *                and w = 4 / (3 rho), rho = max_i sum_j |a_ij| / a_ii;
  *   hierarchy    A_c = P^T A P, repeated until a level has at most
@@ -397,9 +404,12 @@ int ldu_piso_pressure(ldu_matrix *A, const double *coef, double *phi, double *p,
  *   outer        CG (Saad Alg. 9.1) with M^-1 r = V(r), stopping when the
  *                recursive ||r||_2 <= tol ||b||_2 and the true residual
  *                agrees (otherwise the search restarts from it).
- * The hierarchy is built on the host once per matrix; the solve runs
- * entirely in device kernels, its scalars (alpha, beta, the residual norms,
- * the stopping decision) computed and kept on the device. */
+ * The hierarchy is built by device kernels (the host reads only counts
+ * between them, and inverts the coarsest level); every sum of the
+ * construction is formed in a fixed order, so the same matrix always gives
+ * the same hierarchy.  The solve runs entirely in device kernels, its
+ * scalars (alpha, beta, the residual norms, the stopping decision) computed
+ * and kept on the device. */
 typedef struct ldu_amg ldu_amg;   /* opaque AMG hierarchy */
 
 typedef struct amg_opts {
@@ -412,17 +422,18 @@ typedef struct amg_opts {
 } amg_opts;
 
 /* Build the hierarchy of an LDU matrix.  n, nFaces, owner, neighbour,
- * diag, upper, lower: as ldu_create (device arrays, copied to the host and
- * validated there; the hierarchy uses both triangles, the solvers need a
- * symmetric positive definite A).  aopt: host, may be NULL.  The fine level
- * stores A's off-diagonal part in sliced ELL with 32-row slices (plus 16-bit
- * column offsets from the row when every offset fits), coarse levels in CSR;
- * every level keeps its diagonal and w/diagonal, P and R = P^T in CSR, all
- * values in double and in float.  The Galerkin products run on up to 16 host
- * threads (the result does not depend on their number).  Synchronises
- * stream.  Errors as ldu_create; NOT_SPD if the coarsest matrix is singular;
- * UNSUPPORTED if coarsening stops above 4096 rows or a level's entries
- * exceed int32 indexing. */
+ * diag, upper, lower: as ldu_create (device arrays, validated on the
+ * device; the hierarchy uses both triangles, the solvers need a symmetric
+ * positive definite A).  aopt: host, may be NULL.  The fine level stores A's
+ * off-diagonal part in sliced ELL with 32-row slices (plus 16-bit column
+ * offsets from the row when every offset fits), coarse levels in CSR; every
+ * level keeps its diagonal and w/diagonal, P and R = P^T in CSR, all values
+ * in double and in float.  The construction takes temporary device memory
+ * (stream-ordered allocations on `stream`) of the order of the fine matrix
+ * times its rows' product lengths, released before returning.  Synchronises
+ * stream.  Errors as ldu_create; NOT_SPD if a level's diagonal is not
+ * positive or the coarsest matrix is singular; UNSUPPORTED if coarsening
+ * stops above 4096 rows or a level's entries exceed int32 indexing. */
 int ldu_amg_create(int64_t n, int64_t nFaces, const int32_t *owner, const int32_t *neighbour,
                    const double *diag, const double *upper, const double *lower,
                    const amg_opts *aopt, ldu_stream_t stream, ldu_amg **out);
@@ -470,7 +481,9 @@ int amg_pcg_solve(ldu_amg *M, const double *b, double *x, double tol, int maxit,
  * updates z, q, s, p, x, r, u, w and forms (r, u), (w, u), (r, r) together.
  * In exact arithmetic its iterates are amg_pcg_solve's.  Stops on the
  * recursive residual and confirms with the true one (a disagreement
- * restarts the recurrences from it).  Arguments, outputs and errors as
+ * restarts the recurrences from it); a non-positive step denominator after
+ * the first step of a run is rounding drift and takes the same path, only a
+ * non-positive (u, A u) on a fresh start returns NOT_SPD.  Arguments, outputs and errors as
  * amg_pcg_solve (FP64 only).  Allocates seven work vectors on a hierarchy's
  * first call; one iteration is captured and replayed as a CUDA graph as in
  * amg_pcg_solve.  Synchronises stream. */

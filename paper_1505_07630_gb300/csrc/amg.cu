@@ -3,12 +3,12 @@
 // The paper preconditions its CG with a V-cycle of an aggregation-based AMG
 // (aggregates around a distance-2 maximal independent set, weighted-Jacobi
 // smoother with omega = 4/3).  The reading implemented here:
-//   aggregation   rows in increasing order; phase 1: a row whose neighbours
-//                 are all free becomes a root and takes them (roots form a
-//                 greedy distance-2 independent set); phase 2: every free row
-//                 joins the phase-1 aggregate of its strongest neighbour
-//                 (largest |a_ij|, strengths within a relative 1e-12 tie and
-//                 go to the lower aggregate); phase 3: isolated rows alone;
+//   aggregation   roots: a distance-2 maximal independent set formed by
+//                 Luby-style rounds on SplitMix64 priorities (Bell, Dalton &
+//                 Olson 2012, the parallel aggregation of CUSP); rows next to
+//                 a root join it, the rest join their strongest assigned
+//                 neighbour (largest |a_ij|; ties within 1e-12 of the row's
+//                 largest |a_ij| go to the lower aggregate);
 //   prolongator   P = (I - w D^-1 A) P_t, w = 4 / (3 rho), rho the Gershgorin
 //                 bound of D^-1 A (max_i sum_j |a_ij| / a_ii);
 //   coarse        A_c = P^T A P until a level has at most max_coarse rows,
@@ -16,20 +16,24 @@
 //   cycle         V(1,1) with the same weighted Jacobi, from zero;
 //   outer         PCG (Saad Alg. 9.1) with z = V(r), stopping on the
 //                 recursive ||r|| and confirming with the true residual.
-// The hierarchy is built on the host (it runs once per matrix); every step of
-// a solve runs in the kernels below, the scalars of the outer PCG staying on
-// the device, so that the host only reads them between batches of iterations.
+// The hierarchy is built on the device (amg_setup.cuh): aggregation from a
+// distance-2 maximal independent set formed in parallel, smoothed
+// prolongator, transpose and Galerkin product, with the host only reading
+// counts between kernels; every step of a solve runs in the kernels below,
+// the scalars of the outer PCG staying on the device, so that the host only
+// reads them between batches of iterations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
-#include <thread>
 #include <type_traits>
 #include <vector>
 
 #include "ldupcg_impl.cuh"
+#include "amg_setup.cuh"
+#include "setup_kernels.cuh"
 
 using namespace ldu;
 
@@ -52,265 +56,6 @@ struct HCsr {
     std::vector<int32_t> col;       // sorted within each row
     std::vector<double> val;
 };
-
-// both triangles of an LDU matrix, rows sorted, duplicate entries summed
-// (two passes: row lengths, then a fill and a sort of each row's entries)
-HCsr csr_from_ldu(int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
-                  const double *diag, const double *up, const double *lo) {
-    std::vector<int64_t> start((size_t)n + 1, 0);
-    for (int64_t i = 0; i < n; ++i)
-        start[(size_t)i + 1] = 1;
-    for (int64_t f = 0; f < nf; ++f) {
-        ++start[(size_t)own[f] + 1];
-        ++start[(size_t)nbr[f] + 1];
-    }
-    for (int64_t i = 0; i < n; ++i)
-        start[(size_t)i + 1] += start[(size_t)i];
-    std::vector<std::pair<int32_t, double>> ent((size_t)start[(size_t)n]);
-    std::vector<int64_t> at(start.begin(), start.end() - 1);
-    for (int64_t i = 0; i < n; ++i)
-        ent[(size_t)at[(size_t)i]++] = {(int32_t)i, diag[i]};
-    for (int64_t f = 0; f < nf; ++f) {
-        ent[(size_t)at[(size_t)own[f]]++] = {nbr[f], up[f]};
-        ent[(size_t)at[(size_t)nbr[f]]++] = {own[f], lo[f]};
-    }
-    HCsr A;
-    A.n = A.m = n;
-    A.ptr.assign((size_t)n + 1, 0);
-    A.col.reserve(ent.size());
-    A.val.reserve(ent.size());
-    for (int64_t i = 0; i < n; ++i) {
-        auto b = ent.begin() + start[(size_t)i], e = ent.begin() + start[(size_t)i + 1];
-        // stable: entries of one column keep their face order, so duplicates sum in a fixed order
-        std::stable_sort(b, e, [](const std::pair<int32_t, double> &x,
-                                  const std::pair<int32_t, double> &y) { return x.first < y.first; });
-        const size_t row_begin = A.col.size();
-        for (auto it = b; it != e; ++it) {
-            if (A.col.size() > row_begin && it->first == A.col.back()) {
-                A.val.back() += it->second;
-                continue;
-            }
-            A.col.push_back(it->first);
-            A.val.push_back(it->second);
-        }
-        A.ptr[(size_t)i + 1] = (int64_t)A.col.size();
-    }
-    return A;
-}
-
-double diag_of(const HCsr &A, int64_t i) {
-    for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k)
-        if (A.col[(size_t)k] == i)
-            return A.val[(size_t)k];
-    return 0.0;
-}
-
-// phases 1-3 of the aggregation; returns the number of aggregates
-int64_t aggregate(const HCsr &A, std::vector<int32_t> &agg) {
-    const int64_t n = A.n;
-    agg.assign((size_t)n, -1);
-    int64_t na = 0;
-    for (int64_t i = 0; i < n; ++i) {   // phase 1
-        if (agg[(size_t)i] >= 0)
-            continue;
-        bool any = false, free_all = true;
-        for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k) {
-            const int32_t j = A.col[(size_t)k];
-            if (j == i)
-                continue;
-            any = true;
-            if (agg[(size_t)j] >= 0) {
-                free_all = false;
-                break;
-            }
-        }
-        if (!any || !free_all)
-            continue;
-        agg[(size_t)i] = (int32_t)na;
-        for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k)
-            agg[(size_t)A.col[(size_t)k]] = (int32_t)na;
-        ++na;
-    }
-    const std::vector<int32_t> phase1 = agg;
-    for (int64_t i = 0; i < n; ++i) {   // phase 2
-        if (phase1[(size_t)i] >= 0)
-            continue;
-        int32_t best = -1;
-        double best_v = -1.0;
-        for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k) {
-            const int32_t j = A.col[(size_t)k];
-            if (j == i || phase1[(size_t)j] < 0)
-                continue;
-            const double a = std::fabs(A.val[(size_t)k]);
-            if (best < 0 || a > best_v * (1.0 + kTie)) {
-                best = phase1[(size_t)j];
-                best_v = a;
-            } else if (a >= best_v * (1.0 - kTie) && phase1[(size_t)j] < best) {
-                best = phase1[(size_t)j];
-                best_v = std::max(a, best_v);
-            }
-        }
-        agg[(size_t)i] = best;
-    }
-    for (int64_t i = 0; i < n; ++i)     // phase 3
-        if (agg[(size_t)i] < 0)
-            agg[(size_t)i] = (int32_t)na++;
-    return na;
-}
-
-// w = 4 / (3 rho), rho = max_i sum_j |a_ij| / a_ii
-double jacobi_weight(const HCsr &A) {
-    double rho = 0.0;
-    for (int64_t i = 0; i < A.n; ++i) {
-        double s = 0.0;
-        for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k)
-            s += std::fabs(A.val[(size_t)k]);
-        rho = std::max(rho, s / diag_of(A, i));
-    }
-    return 4.0 / (3.0 * rho);
-}
-
-// P = (I - w D^-1 A) P_t: row i holds, for every aggregate J touched by row
-// i of A, [J == agg(i)] - w (1/a_ii) sum_{j in J} a_ij; exact zeros dropped
-HCsr prolongator(const HCsr &A, const std::vector<int32_t> &agg, int64_t na, double w) {
-    HCsr P;
-    P.n = A.n;
-    P.m = na;
-    P.ptr.assign((size_t)A.n + 1, 0);
-    std::vector<std::pair<int32_t, double>> row;
-    for (int64_t i = 0; i < A.n; ++i) {
-        row.clear();
-        for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k) {
-            const int32_t J = agg[(size_t)A.col[(size_t)k]];
-            auto it = std::find_if(row.begin(), row.end(),
-                                   [J](const std::pair<int32_t, double> &e) { return e.first == J; });
-            if (it == row.end())
-                row.push_back({J, A.val[(size_t)k]});
-            else
-                it->second += A.val[(size_t)k];
-        }
-        const double inv_d = 1.0 / diag_of(A, i);
-        const int32_t own_agg = agg[(size_t)i];
-        bool has_own = false;
-        for (auto &e : row) {
-            const double t = w * (inv_d * e.second);
-            e.second = (e.first == own_agg ? 1.0 : 0.0) - t;
-            has_own |= e.first == own_agg;
-        }
-        if (!has_own)
-            row.push_back({own_agg, 1.0});
-        std::sort(row.begin(), row.end(),
-                  [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
-                      return a.first < b.first;
-                  });
-        for (auto &e : row)
-            if (e.second != 0.0) {
-                P.col.push_back(e.first);
-                P.val.push_back(e.second);
-            }
-        P.ptr[(size_t)i + 1] = (int64_t)P.col.size();
-    }
-    return P;
-}
-
-HCsr transpose(const HCsr &P) {
-    HCsr R;
-    R.n = P.m;
-    R.m = P.n;
-    R.ptr.assign((size_t)R.n + 1, 0);
-    for (int32_t c : P.col)
-        ++R.ptr[(size_t)c + 1];
-    for (int64_t I = 0; I < R.n; ++I)
-        R.ptr[(size_t)I + 1] += R.ptr[(size_t)I];
-    R.col.resize(P.col.size());
-    R.val.resize(P.val.size());
-    std::vector<int64_t> at(R.ptr.begin(), R.ptr.end() - 1);
-    for (int64_t i = 0; i < P.n; ++i)   // rows in increasing order: columns of R sorted
-        for (int64_t k = P.ptr[(size_t)i]; k < P.ptr[(size_t)i + 1]; ++k) {
-            const int64_t dst = at[(size_t)P.col[(size_t)k]]++;
-            R.col[(size_t)dst] = (int32_t)i;
-            R.val[(size_t)dst] = P.val[(size_t)k];
-        }
-    return R;
-}
-
-// A_c = R A P with R = P^T, one coarse row at a time through a dense
-// accumulator; exact zeros dropped.  Rows are independent, so blocks of them
-// are formed on several host threads and concatenated in row order: the
-// result does not depend on the thread count.
-HCsr galerkin(const HCsr &A, const HCsr &P, const HCsr &R) {
-    const int64_t nc = P.m;
-    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    if (nc < 4096)
-        nt = 1;
-    struct Part {
-        std::vector<int64_t> len;
-        std::vector<int32_t> col;
-        std::vector<double> val;
-    };
-    std::vector<Part> parts(nt);
-    auto work = [&](unsigned t) {
-        const int64_t lo = nc * t / nt, hi = nc * (t + 1) / nt;
-        Part &out = parts[t];
-        out.len.assign((size_t)(hi - lo), 0);
-        std::vector<double> acc((size_t)nc, 0.0);
-        std::vector<char> used((size_t)nc, 0);
-        std::vector<int32_t> touched;
-        for (int64_t I = lo; I < hi; ++I) {
-            touched.clear();
-            for (int64_t a = R.ptr[(size_t)I]; a < R.ptr[(size_t)I + 1]; ++a) {
-                const int32_t i = R.col[(size_t)a];
-                const double r = R.val[(size_t)a];
-                for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k) {
-                    const int32_t j = A.col[(size_t)k];
-                    const double ra = r * A.val[(size_t)k];
-                    for (int64_t q = P.ptr[(size_t)j]; q < P.ptr[(size_t)j + 1]; ++q) {
-                        const int32_t J = P.col[(size_t)q];
-                        if (!used[(size_t)J]) {
-                            used[(size_t)J] = 1;
-                            touched.push_back(J);
-                        }
-                        acc[(size_t)J] += ra * P.val[(size_t)q];
-                    }
-                }
-            }
-            std::sort(touched.begin(), touched.end());
-            int64_t len = 0;
-            for (int32_t J : touched) {
-                if (acc[(size_t)J] != 0.0) {
-                    out.col.push_back(J);
-                    out.val.push_back(acc[(size_t)J]);
-                    ++len;
-                }
-                acc[(size_t)J] = 0.0;
-                used[(size_t)J] = 0;
-            }
-            out.len[(size_t)(I - lo)] = len;
-        }
-    };
-    if (nt == 1) {
-        work(0);
-    } else {
-        std::vector<std::thread> pool;
-        for (unsigned t = 0; t < nt; ++t)
-            pool.emplace_back(work, t);
-        for (auto &th : pool)
-            th.join();
-    }
-    HCsr Ac;
-    Ac.n = Ac.m = nc;
-    Ac.ptr.assign((size_t)nc + 1, 0);
-    int64_t row = 0;
-    for (const Part &pt : parts) {
-        for (int64_t len : pt.len) {
-            Ac.ptr[(size_t)row + 1] = Ac.ptr[(size_t)row] + len;
-            ++row;
-        }
-        Ac.col.insert(Ac.col.end(), pt.col.begin(), pt.col.end());
-        Ac.val.insert(Ac.val.end(), pt.val.begin(), pt.val.end());
-    }
-    return Ac;
-}
 
 // Gauss-Jordan inverse with partial pivoting (row-major, n x n); false if singular
 bool dense_inverse(const HCsr &A, std::vector<double> &inv) {
@@ -952,7 +697,16 @@ __global__ void __launch_bounds__(kThreads, kUpdateBlocksPerSm) k_pp_update(int 
     double v[3] = {g, dl, rr}, tot[3];
     if (grid_sum_last<3>(v, part, count, tot) && threadIdx.x == 0) {
         if (!ok) {
-            S->status = LDU_ERR_NOT_SPD;
+            if (restart) {   // (u, A u) <= 0 on a fresh start: A is not SPD
+                S->status = LDU_ERR_NOT_SPD;
+                S->done = 1;
+                return;
+            }
+            // the denominator is (p, A p) > 0 in exact arithmetic: a
+            // non-positive one is drift of the recurrences (near the limit
+            // of FP64), so this run ends as a converged one would and the
+            // host confirms it with the true residual, restarting from it
+            S->conv = 1;
             S->done = 1;
             return;
         }
@@ -1046,74 +800,6 @@ cudaError_t alloc(T **dst, int64_t count, int64_t *bytes) {
     return e;
 }
 
-// host sliced-ELL image of A's off-diagonal part
-struct HSell {
-    std::vector<int> sp, sw, col;
-    std::vector<double> val;
-};
-
-// false when the padded slot count does not fit an int
-bool sell_of(const HCsr &A, HSell &S) {
-    const int64_t ns = (A.n + 31) / 32;
-    S.sp.assign((size_t)ns + 1, 0);
-    S.sw.assign((size_t)ns, 0);
-    int64_t total = 0;
-    for (int64_t s = 0; s < ns; ++s) {
-        int w = 0;
-        for (int64_t row = s * 32; row < std::min<int64_t>(A.n, s * 32 + 32); ++row) {
-            int len = 0;
-            for (int64_t k = A.ptr[(size_t)row]; k < A.ptr[(size_t)row + 1]; ++k)
-                len += A.col[(size_t)k] != row;
-            w = std::max(w, len);
-        }
-        S.sw[(size_t)s] = w;
-        total += 32 * (int64_t)w;
-        if (total > INT32_MAX)
-            return false;
-        S.sp[(size_t)s + 1] = (int)total;
-    }
-    S.col.assign((size_t)S.sp.back(), 0);
-    S.val.assign((size_t)S.sp.back(), 0.0);
-    for (int64_t row = 0; row < A.n; ++row) {
-        const int64_t s = row / 32, i = row % 32;
-        int k = 0;
-        for (int64_t e = A.ptr[(size_t)row]; e < A.ptr[(size_t)row + 1]; ++e) {
-            if (A.col[(size_t)e] == row)
-                continue;
-            const size_t at = (size_t)S.sp[(size_t)s] + (size_t)k * 32 + (size_t)i;
-            S.col[at] = A.col[(size_t)e];
-            S.val[at] = A.val[(size_t)e];
-            ++k;
-        }
-    }
-    return true;
-}
-
-// the sliced ELL of A's off-diagonal part with its columns as 16-bit offsets
-// from their rows (padding slots: offset 0, the row itself, whose value is
-// 0); false if some offset does not fit
-bool offsets16(const HCsr &A, const HSell &S, std::vector<short> &c16) {
-    c16.assign(S.col.size(), 0);
-    const int64_t ns = (int64_t)S.sw.size();
-    for (int64_t s = 0; s < ns; ++s)
-        for (int i = 0; i < 32; ++i) {
-            const int64_t row = s * 32 + i;
-            if (row >= A.n)
-                break;
-            int len = 0;   // off-diagonal entries of the row: its first len slots
-            for (int64_t e = A.ptr[(size_t)row]; e < A.ptr[(size_t)row + 1]; ++e)
-                len += A.col[(size_t)e] != row;
-            for (int k = 0; k < len; ++k) {
-                const size_t at = (size_t)S.sp[(size_t)s] + (size_t)k * 32 + (size_t)i;
-                const int64_t off = (int64_t)S.col[at] - row;
-                if (off < -32768 || off > 32767)
-                    return false;
-                c16[at] = (short)off;
-            }
-        }
-    return true;
-}
-
 }  // namespace
 
 // the values and vectors of one level in one precision
@@ -1139,7 +825,7 @@ struct amg_level {
     int64_t r_rows = 0;                       // rows of R (= next level's)
     LevelVals<double> v64;
     LevelVals<float> v32;
-    std::vector<int32_t> agg;                 // host copy, for inspection
+    int *agg = nullptr;                       // aggregate of every row (device)
     template <typename T>
     const LevelVals<T> &v() const;
     template <typename T>
@@ -1213,7 +899,8 @@ void free_amg(ldu_amg *M) {
     if (!M)
         return;
     for (auto &L : M->lev) {
-        void *ptrs[] = {L.a_sp, L.a_sw, L.a_ptr, L.a_col, L.a_c16, L.p_ptr, L.p_col, L.r_ptr, L.r_col};
+        void *ptrs[] = {L.a_sp,  L.a_sw,  L.a_ptr, L.a_col, L.a_c16,
+                        L.p_ptr, L.p_col, L.r_ptr, L.r_col, L.agg};
         for (void *p : ptrs)
             if (p)
                 cudaFree(p);
@@ -1519,6 +1206,468 @@ int pipe_loop(ldu_amg *M, const double *b, double *x, double tol, int maxit, int
     return outer_loop(M, 2, x, tol, maxit, residual, resume, body, iters, relres, st);
 }
 
+// ---- the hierarchy on the device (kernels in amg_setup.cuh) ---------------
+
+// a level's matrix during construction: CSR, the diagonal in every row,
+// columns sorted (n x m; ptr has n + 1 entries)
+struct GCsr {
+    int64_t n = 0, m = 0, nnz = 0;
+    int64_t *ptr = nullptr;
+    int *col = nullptr;
+    double *val = nullptr;
+};
+
+// stream-ordered scratch of the construction, released on every path
+struct Scratch {
+    cudaStream_t st;
+    std::vector<void *> live;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    template <typename T>
+    cudaError_t get(T **p, int64_t count) {
+        *p = nullptr;
+        const cudaError_t e =
+            cudaMallocAsync((void **)p, sizeof(T) * (size_t)std::max<int64_t>(count, 1), st);
+        if (e == cudaSuccess)
+            live.push_back((void *)*p);
+        return e;
+    }
+    void put(const void *p) {
+        for (size_t k = 0; k < live.size(); ++k)
+            if (live[k] == p) {
+                cudaFreeAsync(live[k], st);
+                live.erase(live.begin() + (long)k);
+                return;
+            }
+    }
+    void put(GCsr &A) {
+        put(A.ptr);
+        put(A.col);
+        put(A.val);
+        A = GCsr();
+    }
+    ~Scratch() {
+        for (void *p : live)
+            cudaFreeAsync(p, st);
+    }
+};
+
+#define CKS(call)                           \
+    do {                                    \
+        const cudaError_t e_ = (call);      \
+        if (e_ != cudaSuccess)              \
+            return cuda_status(e_);         \
+    } while (0)
+#define LAUNCHED() CKS(cudaGetLastError())
+
+// out = exclusive scan of in[0..n) (n + 1 entries); *total = out[n]
+int exscan(Scratch &S, const int64_t *in, int64_t n, int64_t **out, int64_t *total) {
+    int64_t *tmp;
+    CKS(S.get(out, n + 1));
+    CKS(S.get(&tmp, amgs::scan_tmp_items(n)));
+    amgs::scan_excl(in, *out, n, tmp, S.st);
+    LAUNCHED();
+    CKS(cudaMemcpyAsync(total, *out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, S.st));
+    CKS(cudaStreamSynchronize(S.st));
+    S.put(tmp);
+    return LDU_OK;
+}
+
+int read_int(Scratch &S, const int *dev, int *host) {
+    CKS(cudaMemcpyAsync(host, dev, sizeof(int), cudaMemcpyDeviceToHost, S.st));
+    CKS(cudaStreamSynchronize(S.st));
+    return LDU_OK;
+}
+
+// both triangles of an LDU matrix with the diagonal; entries of one column
+// (duplicate faces) added in face order
+int ldu_to_csr(Scratch &S, int64_t n, int64_t nf, const int32_t *own, const int32_t *nbr,
+               const double *diag, const double *up, const double *lo, GCsr &A) {
+    using namespace amgs;
+    int64_t *len, *xptr, *xkey, *cur, xnnz = 0;
+    int *xcol;
+    double *xval;
+    CKS(S.get(&len, n));
+    k_ones<<<blocks(n), kT, 0, S.st>>>(n, len);
+    if (nf > 0)
+        k_ldu_len<<<blocks(nf), kT, 0, S.st>>>(nf, own, nbr, len);
+    LAUNCHED();
+    if (int rc = exscan(S, len, n, &xptr, &xnnz))
+        return rc;
+    CKS(S.get(&xcol, xnnz));
+    CKS(S.get(&xval, xnnz));
+    CKS(S.get(&xkey, xnnz));
+    CKS(S.get(&cur, n));
+    k_ldu_fill_diag<<<blocks(n), kT, 0, S.st>>>(n, xptr, diag, xcol, xval, xkey, cur);
+    if (nf > 0)
+        k_ldu_fill_faces<<<blocks(nf), kT, 0, S.st>>>(nf, own, nbr, up, lo, xcol, xval, xkey,
+                                                       cur);
+    k_row_sort_merge<<<blocks(n), kT, 0, S.st>>>(n, xptr, xcol, xval, xkey, len);
+    LAUNCHED();
+    A.n = A.m = n;
+    if (int rc = exscan(S, len, n, &A.ptr, &A.nnz))
+        return rc;
+    CKS(S.get(&A.col, A.nnz));
+    CKS(S.get(&A.val, A.nnz));
+    k_pack<<<blocks(n), kT, 0, S.st>>>(n, xptr, xcol, xval, A.ptr, A.col, A.val);
+    LAUNCHED();
+    for (const void *p : {(const void *)len, (const void *)xptr, (const void *)xkey,
+                          (const void *)cur, (const void *)xcol, (const void *)xval})
+        S.put(p);
+    return LDU_OK;
+}
+
+// Z = X Y on the structural pattern, each row summed in a fixed order
+int spgemm(Scratch &S, const GCsr &X, const GCsr &Y, GCsr &Z) {
+    using namespace amgs;
+    const int n = (int)X.n;
+    int64_t *ub, *ts, *tp, *cnt, tsize = 0;
+    int *tcol;
+    double *tval;
+    CKS(S.get(&ub, n));
+    CKS(S.get(&ts, n));
+    k_gemm_bound<<<blocks(n), kT, 0, S.st>>>(n, X.ptr, X.col, Y.ptr, ub);
+    k_gemm_tsize<<<blocks(n), kT, 0, S.st>>>(n, ub, ts);
+    LAUNCHED();
+    if (int rc = exscan(S, ts, n, &tp, &tsize))
+        return rc;
+    CKS(S.get(&tcol, tsize));
+    CKS(S.get(&tval, tsize));
+    CKS(S.get(&cnt, n));
+    k_gemm_rows<<<blocks(n), kT, 0, S.st>>>(n, X.ptr, X.col, X.val, Y.ptr, Y.col, Y.val, tp, tcol,
+                                            tval, cnt);
+    LAUNCHED();
+    Z.n = X.n;
+    Z.m = Y.m;
+    if (int rc = exscan(S, cnt, n, &Z.ptr, &Z.nnz))
+        return rc;
+    CKS(S.get(&Z.col, Z.nnz));
+    CKS(S.get(&Z.val, Z.nnz));
+    k_pack<<<blocks(n), kT, 0, S.st>>>(n, tp, tcol, tval, Z.ptr, Z.col, Z.val);
+    LAUNCHED();
+    for (const void *p : {(const void *)ub, (const void *)ts, (const void *)tp, (const void *)cnt,
+                          (const void *)tcol, (const void *)tval})
+        S.put(p);
+    return LDU_OK;
+}
+
+// a kept copy (cudaMalloc, counted) of a device array
+template <typename T>
+int keep_copy(Scratch &S, T **dst, const T *src, int64_t count, int64_t *nb) {
+    CKS(alloc(dst, count, nb));
+    if (count > 0)
+        CKS(cudaMemcpyAsync(*dst, src, sizeof(T) * (size_t)count, cudaMemcpyDeviceToDevice, S.st));
+    return LDU_OK;
+}
+
+// a kept int32 copy of an int64 array (values checked to fit by the caller)
+int keep_i32(Scratch &S, int **dst, const int64_t *src, int64_t count, int64_t *nb) {
+    CKS(alloc(dst, count, nb));
+    amgs::k_i64_to_i32<<<amgs::blocks(count), amgs::kT, 0, S.st>>>(count, src, *dst);
+    LAUNCHED();
+    return LDU_OK;
+}
+
+// kept double values and their float rounding
+int keep_vals(Scratch &S, double **d64, float **d32, const double *src, int64_t count,
+              int64_t *nb) {
+    if (int rc = keep_copy(S, d64, src, count, nb))
+        return rc;
+    CKS(alloc(d32, count, nb));
+    amgs::k_d2f<<<amgs::blocks(count), amgs::kT, 0, S.st>>>(count, *d64, *d32);
+    LAUNCHED();
+    return LDU_OK;
+}
+
+// A's off-diagonal part in 32-row sliced ELL, kept: slice offsets and widths,
+// columns, double values (the float copy is left to the caller) and, when
+// every column lies within 16 bits of its row, the offsets; *padded = slots.
+// Returns UNSUPPORTED when the slots exceed int32 indexing.  With probe, only
+// *padded is computed.
+int sell32(Scratch &S, const GCsr &A, const int64_t *olen, bool probe, int64_t *padded,
+           int **sp, int **sw, int **col, double **val, short **c16, int64_t *nb) {
+    using namespace amgs;
+    const int n = (int)A.n;
+    const int64_t ns = (A.n + 31) / 32;
+    int64_t *swd, *slots, *spd;
+    CKS(S.get(&swd, ns));
+    CKS(S.get(&slots, ns));
+    k_slice32_width<<<blocks(ns), kT, 0, S.st>>>(n, olen, swd);
+    k_slice32_slots<<<blocks(ns), kT, 0, S.st>>>((int)ns, swd, slots);
+    LAUNCHED();
+    if (int rc = exscan(S, slots, ns, &spd, padded))
+        return rc;
+    if (!probe) {
+        if (*padded > INT32_MAX)
+            return LDU_ERR_UNSUPPORTED;
+        int *flags;
+        CKS(S.get(&flags, 1));
+        CKS(cudaMemsetAsync(flags, 0, sizeof(int), S.st));
+        CKS(alloc(col, *padded, nb));
+        CKS(alloc(val, *padded, nb));
+        CKS(alloc(c16, *padded, nb));
+        k_sell32_fill<<<blocks(ns * 32), kT, 0, S.st>>>(n, A.ptr, A.col, A.val, spd, swd, *col,
+                                                        *val, *c16, flags);
+        LAUNCHED();
+        if (int rc = keep_i32(S, sp, spd, ns + 1, nb))
+            return rc;
+        if (int rc = keep_i32(S, sw, swd, ns, nb))
+            return rc;
+        int hf = 0;
+        if (int rc = read_int(S, flags, &hf))
+            return rc;
+        if (hf & 4) {   // some column is beyond 16 bits of its row
+            cudaFree(*c16);
+            *nb -= (int64_t)sizeof(short) * std::max<int64_t>(*padded, 1);
+            *c16 = nullptr;
+        }
+        S.put(flags);
+    }
+    S.put(swd);
+    S.put(slots);
+    S.put(spd);
+    return LDU_OK;
+}
+
+// One level: its scalars, aggregates, P, R and device layouts (kept in L)
+// and its Galerkin matrix Ac.  *stop = true when the aggregation would not
+// shrink the level (nothing is kept then).
+int build_level(Scratch &S, const GCsr &A, bool first, int lanes, amg_level &L, GCsr &Ac,
+                bool *stop, int64_t *nb) {
+    using namespace amgs;
+    const int n = (int)A.n;
+    *stop = false;
+    // 1. d, rho, w
+    double *d;
+    unsigned long long *rho_bits;
+    int *flags;
+    CKS(S.get(&d, n));
+    CKS(S.get(&rho_bits, 1));
+    CKS(S.get(&flags, 1));
+    CKS(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), S.st));
+    CKS(cudaMemsetAsync(flags, 0, sizeof(int), S.st));
+    k_diag_rho<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, A.col, A.val, d, rho_bits, flags);
+    LAUNCHED();
+    unsigned long long rb = 0;
+    int hf = 0;
+    CKS(cudaMemcpyAsync(&rb, rho_bits, sizeof(rb), cudaMemcpyDeviceToHost, S.st));
+    if (int rc = read_int(S, flags, &hf))
+        return rc;
+    if (hf & 1)
+        return LDU_ERR_NOT_SPD;
+    double rho;
+    std::memcpy(&rho, &rb, sizeof(rho));
+    const double w = 4.0 / (3.0 * rho);
+    // 2. distance-2 maximal independent set
+    int *state, *s1, *s2;
+    uint64_t *h, *h1, *h2;
+    unsigned *left;
+    CKS(S.get(&state, n));
+    CKS(S.get(&s1, n));
+    CKS(S.get(&s2, n));
+    CKS(S.get(&h, n));
+    CKS(S.get(&h1, n));
+    CKS(S.get(&h2, n));
+    CKS(S.get(&left, 1));
+    k_mis_init<<<blocks(n), kT, 0, S.st>>>(n, state, h);
+    for (int round = 0;; ++round) {
+        if (round > n + 1)
+            return LDU_ERR_UNSUPPORTED;   // every round decides at least one row
+        CKS(cudaMemsetAsync(left, 0, sizeof(unsigned), S.st));
+        k_pair_max<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, A.col, state, h, s1, h1);
+        k_pair_max<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, A.col, s1, h1, s2, h2);
+        k_mis_update<<<blocks(n), kT, 0, S.st>>>(n, state, h, s2, h2, left);
+        LAUNCHED();
+        unsigned hl = 0;
+        CKS(cudaMemcpyAsync(&hl, left, sizeof(hl), cudaMemcpyDeviceToHost, S.st));
+        CKS(cudaStreamSynchronize(S.st));
+        if (hl == 0)
+            break;
+    }
+    // 3. aggregates
+    int64_t *flag, *rank, na = 0;
+    CKS(S.get(&flag, n));
+    k_root_flags<<<blocks(n), kT, 0, S.st>>>(n, state, flag);
+    LAUNCHED();
+    if (int rc = exscan(S, flag, n, &rank, &na))
+        return rc;
+    if (na >= n) {
+        *stop = true;
+        return LDU_OK;
+    }
+    int *firsta, *agg;
+    CKS(S.get(&firsta, n));
+    CKS(alloc(&agg, n, nb));
+    L.agg = agg;
+    k_agg_roots<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, A.col, state, rank, firsta);
+    k_agg_rest<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, A.col, A.val, firsta, agg, kTie, flags);
+    LAUNCHED();
+    if (int rc = read_int(S, flags, &hf))
+        return rc;
+    if (hf & 2)
+        return LDU_ERR_UNSUPPORTED;   // a row beyond two steps of every root: not a maximal set
+    for (const void *p : {(const void *)state, (const void *)s1, (const void *)s2,
+                          (const void *)h, (const void *)h1, (const void *)h2, (const void *)left,
+                          (const void *)flag, (const void *)rank, (const void *)firsta})
+        S.put(p);
+    // 4. P = (I - w D^-1 A) P_t on the pattern of (I + A) P_t
+    GCsr P;
+    {
+        int *xcol;
+        double *xval;
+        int64_t *xkey, *cnt;
+        CKS(S.get(&xcol, A.nnz));
+        CKS(S.get(&xval, A.nnz));
+        CKS(S.get(&xkey, A.nnz));
+        CKS(S.get(&cnt, n));
+        k_p_expand<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, A.col, A.val, agg, xcol, xval, xkey);
+        k_row_sort_merge<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, xcol, xval, xkey, cnt);
+        k_p_values<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, cnt, xcol, xval, agg, d, w);
+        LAUNCHED();
+        P.n = n;
+        P.m = na;
+        if (int rc = exscan(S, cnt, n, &P.ptr, &P.nnz))
+            return rc;
+        CKS(S.get(&P.col, P.nnz));
+        CKS(S.get(&P.val, P.nnz));
+        k_pack<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, xcol, xval, P.ptr, P.col, P.val);
+        LAUNCHED();
+        for (const void *p : {(const void *)xcol, (const void *)xval, (const void *)xkey,
+                              (const void *)cnt})
+            S.put(p);
+    }
+    if (P.nnz > INT32_MAX)
+        return LDU_ERR_UNSUPPORTED;
+    // 5. R = P^T (rows in increasing order within each of its rows)
+    GCsr R;
+    {
+        int64_t *rlen, *cur, *rkey;
+        CKS(S.get(&rlen, na));
+        CKS(cudaMemsetAsync(rlen, 0, sizeof(int64_t) * (size_t)na, S.st));
+        k_col_count<<<blocks(P.nnz), kT, 0, S.st>>>(P.nnz, P.col, rlen);
+        LAUNCHED();
+        R.n = na;
+        R.m = n;
+        if (int rc = exscan(S, rlen, na, &R.ptr, &R.nnz))
+            return rc;
+        CKS(S.get(&cur, na));
+        CKS(S.get(&R.col, R.nnz));
+        CKS(S.get(&R.val, R.nnz));
+        CKS(S.get(&rkey, R.nnz));
+        k_copy_i64<<<blocks(na), kT, 0, S.st>>>(na, R.ptr, cur);
+        k_transpose_fill<<<blocks(n), kT, 0, S.st>>>(n, P.ptr, P.col, P.val, cur, R.col, R.val,
+                                                      rkey);
+        k_row_sort_merge<<<blocks(na), kT, 0, S.st>>>(na, R.ptr, R.col, R.val, rkey, rlen);
+        LAUNCHED();
+        for (const void *p : {(const void *)rlen, (const void *)cur, (const void *)rkey})
+            S.put(p);
+    }
+    // 6. Ac = R (A P)
+    {
+        GCsr AP;
+        if (int rc = spgemm(S, A, P, AP))
+            return rc;
+        if (int rc = spgemm(S, R, AP, Ac))
+            return rc;
+        S.put(AP);
+    }
+    // 7. the level's device layouts
+    L.n = A.n;
+    L.nnz = A.nnz;
+    L.w = w;
+    int64_t *olen;
+    CKS(S.get(&olen, n));
+    k_offdiag_len<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, A.col, olen);
+    LAUNCHED();
+    const int64_t off_nnz = A.nnz - A.n;
+    int64_t padded = 0;
+    if (int rc = sell32(S, A, olen, true, &padded, nullptr, nullptr, nullptr, nullptr, nullptr, nb))
+        return rc;
+    L.a_sell = first || (double)padded <= kSellPad * (double)off_nnz;
+    if (L.a_sell) {
+        if (int rc = sell32(S, A, olen, false, &padded, &L.a_sp, &L.a_sw, &L.a_col, &L.v64.a_val,
+                            &L.a_c16, nb))
+            return rc;
+        CKS(alloc(&L.v32.a_val, padded, nb));
+        k_d2f<<<blocks(padded), kT, 0, S.st>>>(padded, L.v64.a_val, L.v32.a_val);
+        LAUNCHED();
+    } else {
+        int64_t *optr, ototal = 0;
+        if (int rc = exscan(S, olen, n, &optr, &ototal))
+            return rc;
+        if (ototal > INT32_MAX)
+            return LDU_ERR_UNSUPPORTED;
+        CKS(alloc(&L.a_col, ototal, nb));
+        CKS(alloc(&L.v64.a_val, ototal, nb));
+        k_offdiag_csr<<<blocks(n), kT, 0, S.st>>>(n, A.ptr, A.col, A.val, optr, L.a_col,
+                                                   L.v64.a_val);
+        LAUNCHED();
+        if (int rc = keep_i32(S, &L.a_ptr, optr, n + 1, nb))
+            return rc;
+        CKS(alloc(&L.v32.a_val, ototal, nb));
+        k_d2f<<<blocks(ototal), kT, 0, S.st>>>(ototal, L.v64.a_val, L.v32.a_val);
+        LAUNCHED();
+        L.a_lpr = lanes ? lanes : lpr_for(A.n, ototal);
+        S.put(optr);
+    }
+    S.put(olen);
+    {
+        double *wd;
+        CKS(S.get(&wd, n));
+        k_wd<<<blocks(n), kT, 0, S.st>>>(n, d, w, wd);
+        LAUNCHED();
+        if (int rc = keep_vals(S, &L.v64.d, &L.v32.d, d, n, nb))
+            return rc;
+        if (int rc = keep_vals(S, &L.v64.wd, &L.v32.wd, wd, n, nb))
+            return rc;
+        S.put(wd);
+    }
+    if (int rc = keep_i32(S, &L.p_ptr, P.ptr, P.n + 1, nb))
+        return rc;
+    if (int rc = keep_copy(S, &L.p_col, P.col, P.nnz, nb))
+        return rc;
+    if (int rc = keep_vals(S, &L.v64.p_val, &L.v32.p_val, P.val, P.nnz, nb))
+        return rc;
+    if (int rc = keep_i32(S, &L.r_ptr, R.ptr, R.n + 1, nb))
+        return rc;
+    if (int rc = keep_copy(S, &L.r_col, R.col, R.nnz, nb))
+        return rc;
+    if (int rc = keep_vals(S, &L.v64.r_val, &L.v32.r_val, R.val, R.nnz, nb))
+        return rc;
+    L.p_lpr = lpr_for(P.n, P.nnz);
+    L.r_lpr = lanes ? lanes : lpr_for(R.n, R.nnz);
+    L.r_rows = R.n;
+    S.put(P);
+    S.put(R);
+    S.put(d);
+    S.put(rho_bits);
+    S.put(flags);
+    return LDU_OK;
+}
+
+// a device CSR copied to the host (for the coarsest level's dense inverse)
+int to_host(Scratch &S, const GCsr &A, HCsr &H) {
+    H.n = A.n;
+    H.m = A.m;
+    H.ptr.resize((size_t)A.n + 1);
+    H.col.resize((size_t)A.nnz);
+    H.val.resize((size_t)A.nnz);
+    CKS(cudaMemcpyAsync(H.ptr.data(), A.ptr, sizeof(int64_t) * H.ptr.size(),
+                        cudaMemcpyDeviceToHost, S.st));
+    if (A.nnz > 0) {
+        CKS(cudaMemcpyAsync(H.col.data(), A.col, sizeof(int) * H.col.size(),
+                            cudaMemcpyDeviceToHost, S.st));
+        CKS(cudaMemcpyAsync(H.val.data(), A.val, sizeof(double) * H.val.size(),
+                            cudaMemcpyDeviceToHost, S.st));
+    }
+    CKS(cudaStreamSynchronize(S.st));
+    return LDU_OK;
+}
+
+#undef LAUNCHED
+#undef CKS
+
 }  // namespace
 
 extern "C" {
@@ -1545,181 +1694,150 @@ int ldu_amg_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *n
     if (n > INT32_MAX / 2 || nf > INT32_MAX / 2)
         return LDU_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
-    // a host copy of the fine matrix, validated as ldu_create does
-    std::vector<int32_t> ho((size_t)nf), hn((size_t)nf);
-    std::vector<double> hd((size_t)n), hu((size_t)nf), hl((size_t)nf);
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess && nf > 0) {
-        e = cudaMemcpy(ho.data(), owner, sizeof(int32_t) * nf, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(hn.data(), neighbour, sizeof(int32_t) * nf, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(hu.data(), upper, sizeof(double) * nf, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(hl.data(), lower, sizeof(double) * nf, cudaMemcpyDeviceToHost);
-    }
-    if (e == cudaSuccess)
-        e = cudaMemcpy(hd.data(), diag, sizeof(double) * n, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess)
-        return cuda_status(e);
-    for (int64_t f = 0; f < nf; ++f) {
-        const int32_t o = ho[(size_t)f], b = hn[(size_t)f];
-        if (o < 0 || b < 0 || o >= n || b >= n || o >= b)
-            return LDU_ERR_BAD_ADDRESSING;
-        if (!std::isfinite(hu[(size_t)f]) || !std::isfinite(hl[(size_t)f]))
-            return LDU_ERR_NOT_SPD;
-    }
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(hd[(size_t)i]) || !(hd[(size_t)i] > 0.0))
-            return LDU_ERR_NOT_SPD;
-    HCsr A = csr_from_ldu(n, nf, ho.data(), hn.data(), hd.data(), hu.data(), hl.data());
-    std::vector<int32_t>().swap(ho);
-    std::vector<int32_t>().swap(hn);
-
     ldu_amg *M = new ldu_amg();
-    cudaGetDevice(&M->device);
-    M->n = n;
-#define CKA(call)                  \
-    do {                           \
-        e = (call);                \
-        if (e != cudaSuccess) {    \
-            free_amg(M);           \
-            return cuda_status(e); \
-        }                          \
+    int rc = LDU_OK;
+    {
+        Scratch S(st);
+#define CKA(call)                              \
+    do {                                       \
+        const cudaError_t e_ = (call);         \
+        if (e_ != cudaSuccess) {               \
+            rc = cuda_status(e_);              \
+            goto done;                         \
+        }                                      \
     } while (0)
-    int64_t *nb = &M->device_bytes;
-    // coarsen while the level is above max_coarse rows and aggregation shrinks it
-    while (A.n > max_coarse && (int)M->lev.size() < max_levels) {
-        std::vector<int32_t> agg;
-        const int64_t na = aggregate(A, agg);
-        if (na >= A.n)
-            break;
-        M->lev.emplace_back();
-        amg_level &L = M->lev.back();
-        L.n = A.n;
-        L.nnz = (int64_t)A.col.size();
-        L.w = jacobi_weight(A);
-        HCsr P = prolongator(A, agg, na, L.w);
-        HCsr R = transpose(P);
-        if ((int64_t)P.col.size() > INT32_MAX) {
-            free_amg(M);
-            return LDU_ERR_UNSUPPORTED;
-        }
-        HCsr Ac = galerkin(A, P, R);
-        L.agg = std::move(agg);
-        std::vector<double> d((size_t)A.n), wd((size_t)A.n);
-        for (int64_t i = 0; i < A.n; ++i) {
-            d[(size_t)i] = diag_of(A, i);
-            wd[(size_t)i] = L.w / d[(size_t)i];
-        }
-        HSell S;
-        if (!sell_of(A, S)) {
-            free_amg(M);
-            return LDU_ERR_UNSUPPORTED;
-        }
-        const int64_t off_nnz = (int64_t)A.col.size() - A.n;
-        L.a_sell = M->lev.size() == 1 || (double)S.sp.back() <= kSellPad * (double)off_nnz;
-        if (L.a_sell) {
-            CKA(upload(&L.a_sp, S.sp, nb));
-            CKA(upload(&L.a_sw, S.sw, nb));
-            CKA(upload(&L.a_col, S.col, nb));
-            std::vector<short> c16;
-            if (offsets16(A, S, c16))
-                CKA(upload(&L.a_c16, c16, nb));
-            CKA(upload2(&L.v64.a_val, &L.v32.a_val, S.val, nb));
-        } else {
-            // off-diagonal CSR of a coarse level
-            std::vector<int> ap((size_t)A.n + 1, 0), ac;
-            std::vector<double> av;
-            ac.reserve(A.col.size());
-            av.reserve(A.col.size());
-            for (int64_t i = 0; i < A.n; ++i) {
-                for (int64_t k = A.ptr[(size_t)i]; k < A.ptr[(size_t)i + 1]; ++k)
-                    if (A.col[(size_t)k] != i) {
-                        ac.push_back(A.col[(size_t)k]);
-                        av.push_back(A.val[(size_t)k]);
-                    }
-                ap[(size_t)i + 1] = (int)ac.size();
+#define RCA(call)                              \
+    do {                                       \
+        rc = (call);                           \
+        if (rc != LDU_OK)                      \
+            goto done;                         \
+    } while (0)
+        int64_t *nb = &M->device_bytes;
+        GCsr A;
+        std::vector<double> inv;
+        HCsr C;
+        CKA(cudaGetDevice(&M->device));
+        M->n = n;
+        {
+            // validation on the device, as ldu_create does
+            int *deg, *flags;
+            CKA(S.get(&deg, n));
+            CKA(S.get(&flags, 4));
+            CKA(cudaMemsetAsync(deg, 0, sizeof(int) * (size_t)n, st));
+            CKA(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+            if (nf > 0)
+                k_validate_count<<<amgs::blocks(nf), 256, 0, st>>>(nf, (int)n, owner, neighbour,
+                                                                    deg, flags);
+            k_validate_values<<<amgs::blocks(std::max(n, nf)), 256, 0, st>>>(n, nf, diag, upper,
+                                                                              lower, flags);
+            CKA(cudaGetLastError());
+            int hf = 0;
+            RCA(read_int(S, flags, &hf));
+            if (hf & (kFlagBadIndex | kFlagBadOrder)) {
+                rc = LDU_ERR_BAD_ADDRESSING;
+                goto done;
             }
-            if ((int64_t)ac.size() > INT32_MAX) {
-                free_amg(M);
-                return LDU_ERR_UNSUPPORTED;
+            if (hf & (kFlagBadDiag | kFlagNonFinite)) {
+                rc = LDU_ERR_NOT_SPD;
+                goto done;
             }
-            L.a_lpr = lanes ? lanes : lpr_for(A.n, (int64_t)ac.size());
-            CKA(upload(&L.a_ptr, ap, nb));
-            CKA(upload(&L.a_col, ac, nb));
-            CKA(upload2(&L.v64.a_val, &L.v32.a_val, av, nb));
+            S.put(deg);
+            S.put(flags);
         }
-        L.p_lpr = lpr_for(P.n, (int64_t)P.col.size());
-        L.r_lpr = lanes ? lanes : lpr_for(R.n, (int64_t)R.col.size());
-        L.r_rows = R.n;
-        std::vector<int> pp(P.ptr.begin(), P.ptr.end()), rp(R.ptr.begin(), R.ptr.end());
-        CKA(upload2(&L.v64.d, &L.v32.d, d, nb));
-        CKA(upload2(&L.v64.wd, &L.v32.wd, wd, nb));
-        CKA(upload(&L.p_ptr, pp, nb));
-        CKA(upload(&L.p_col, P.col, nb));
-        CKA(upload2(&L.v64.p_val, &L.v32.p_val, P.val, nb));
-        CKA(upload(&L.r_ptr, rp, nb));
-        CKA(upload(&L.r_col, R.col, nb));
-        CKA(upload2(&L.v64.r_val, &L.v32.r_val, R.val, nb));
-        CKA(alloc(&L.v64.t, L.n, nb));
-        CKA(alloc(&L.v64.r, L.n, nb));
-        CKA(alloc(&L.v32.t, L.n, nb));
-        CKA(alloc(&L.v32.r, L.n, nb));
-        if (M->lev.size() > 1) {
-            CKA(alloc(&L.v64.x, L.n, nb));
-            CKA(alloc(&L.v64.b, L.n, nb));
-            CKA(alloc(&L.v32.x, L.n, nb));
-            CKA(alloc(&L.v32.b, L.n, nb));
+        RCA(ldu_to_csr(S, n, nf, owner, neighbour, diag, upper, lower, A));
+        // coarsen while the level is above max_coarse rows and aggregation shrinks it
+        while (A.n > max_coarse && (int)M->lev.size() < max_levels) {
+            M->lev.emplace_back();
+            GCsr Ac;
+            bool stop = false;
+            RCA(build_level(S, A, M->lev.size() == 1, lanes, M->lev.back(), Ac, &stop, nb));
+            if (stop) {
+                M->lev.pop_back();
+                break;
+            }
+            amg_level &L = M->lev.back();
+            CKA(alloc(&L.v64.t, L.n, nb));
+            CKA(alloc(&L.v64.r, L.n, nb));
+            CKA(alloc(&L.v32.t, L.n, nb));
+            CKA(alloc(&L.v32.r, L.n, nb));
+            if (M->lev.size() > 1) {
+                CKA(alloc(&L.v64.x, L.n, nb));
+                CKA(alloc(&L.v64.b, L.n, nb));
+                CKA(alloc(&L.v32.x, L.n, nb));
+                CKA(alloc(&L.v32.b, L.n, nb));
+            }
+            S.put(A);
+            A = Ac;
         }
-        A = std::move(Ac);
-    }
-    if (M->lev.empty()) {
-        // the fine matrix is the coarsest: keep its SpMV form for the outer loop
-        HSell S;
-        if (!sell_of(A, S)) {
-            free_amg(M);
-            return LDU_ERR_UNSUPPORTED;
+        if (M->lev.empty()) {
+            // the fine matrix is the coarsest: keep its SpMV form for the outer loop
+            int64_t *olen, padded = 0;
+            short *c16 = nullptr;
+            CKA(S.get(&olen, A.n));
+            amgs::k_offdiag_len<<<amgs::blocks(A.n), amgs::kT, 0, st>>>((int)A.n, A.ptr, A.col,
+                                                                         olen);
+            CKA(cudaGetLastError());
+            RCA(sell32(S, A, olen, false, &padded, &M->f_sp, &M->f_sw, &M->f_col, &M->f_val,
+                       &c16, nb));
+            if (c16) {
+                cudaFree(c16);
+                *nb -= (int64_t)sizeof(short) * std::max<int64_t>(padded, 1);
+            }
+            unsigned long long *rho_bits;
+            int *flags;
+            CKA(S.get(&rho_bits, 1));
+            CKA(S.get(&flags, 1));
+            CKA(cudaMemsetAsync(rho_bits, 0, sizeof(unsigned long long), st));
+            CKA(cudaMemsetAsync(flags, 0, sizeof(int), st));
+            CKA(alloc(&M->f_d, A.n, nb));
+            amgs::k_diag_rho<<<amgs::blocks(A.n), amgs::kT, 0, st>>>((int)A.n, A.ptr, A.col, A.val,
+                                                                      M->f_d, rho_bits, flags);
+            CKA(cudaGetLastError());
+            S.put(olen);
         }
-        std::vector<double> d((size_t)A.n);
-        for (int64_t i = 0; i < A.n; ++i)
-            d[(size_t)i] = diag_of(A, i);
-        CKA(upload(&M->f_sp, S.sp, nb));
-        CKA(upload(&M->f_sw, S.sw, nb));
-        CKA(upload(&M->f_col, S.col, nb));
-        CKA(upload(&M->f_val, S.val, nb));
-        CKA(upload(&M->f_d, d, nb));
-    }
-    // the coarsest level, applied through its dense inverse
-    if (A.n > kMaxCoarse) {
-        free_amg(M);   // coarsening stopped above what a dense inverse allows
-        return LDU_ERR_UNSUPPORTED;
-    }
-    M->nc = A.n;
-    M->c_nnz = (int64_t)A.col.size();
-    std::vector<double> inv;
-    if (!dense_inverse(A, inv)) {
-        free_amg(M);
-        return LDU_ERR_NOT_SPD;
-    }
-    CKA(upload2(&M->c64.inv, &M->c32.inv, inv, nb));
-    CKA(alloc(&M->c64.x, A.n, nb));
-    CKA(alloc(&M->c64.b, A.n, nb));
-    CKA(alloc(&M->c32.x, A.n, nb));
-    CKA(alloc(&M->c32.b, A.n, nb));
-    CKA(alloc(&M->r, n, nb));
-    CKA(alloc(&M->z, n, nb));
-    CKA(alloc(&M->p, n, nb));
-    CKA(alloc(&M->q, n, nb));
-    CKA(alloc(&M->r32, n, nb));
-    CKA(alloc(&M->z32, n, nb));
-    CKA(alloc(&M->part, 3 * kMaxBlocks, nb));
-    CKA(alloc(&M->count, 1, nb));
-    CKA(cudaMemset(M->count, 0, sizeof(unsigned)));
-    CKA(alloc(&M->S, 1, nb));
-    CKA(cudaMallocHost((void **)&M->S_host, sizeof(AmgScalars)));
-    CKA(cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
+        // the coarsest level, applied through its dense inverse
+        if (A.n > kMaxCoarse) {
+            rc = LDU_ERR_UNSUPPORTED;   // coarsening stopped above what a dense inverse allows
+            goto done;
+        }
+        M->nc = A.n;
+        M->c_nnz = A.nnz;
+        RCA(to_host(S, A, C));
+        if (!dense_inverse(C, inv)) {
+            rc = LDU_ERR_NOT_SPD;
+            goto done;
+        }
+        CKA(upload2(&M->c64.inv, &M->c32.inv, inv, nb));
+        CKA(alloc(&M->c64.x, A.n, nb));
+        CKA(alloc(&M->c64.b, A.n, nb));
+        CKA(alloc(&M->c32.x, A.n, nb));
+        CKA(alloc(&M->c32.b, A.n, nb));
+        CKA(alloc(&M->r, n, nb));
+        CKA(alloc(&M->z, n, nb));
+        CKA(alloc(&M->p, n, nb));
+        CKA(alloc(&M->q, n, nb));
+        CKA(alloc(&M->r32, n, nb));
+        CKA(alloc(&M->z32, n, nb));
+        CKA(alloc(&M->part, 3 * kMaxBlocks, nb));
+        CKA(alloc(&M->count, 1, nb));
+        CKA(cudaMemset(M->count, 0, sizeof(unsigned)));
+        CKA(alloc(&M->S, 1, nb));
+        CKA(cudaMallocHost((void **)&M->S_host, sizeof(AmgScalars)));
+        CKA(cudaStreamCreateWithFlags(&M->cap, cudaStreamNonBlocking));
 #undef CKA
+#undef RCA
+    done:;
+    }   // the scratch is released here (stream-ordered)
+    if (rc == LDU_OK) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess)
+            rc = cuda_status(e);
+    }
+    if (rc != LDU_OK) {
+        cudaStreamSynchronize(st);
+        free_amg(M);
+        return rc;
+    }
     *out = M;
     return LDU_OK;
 }
@@ -1748,9 +1866,10 @@ int ldu_amg_info(const ldu_amg *M, int *levels, int64_t *rows, int64_t *nnz, int
 int ldu_amg_aggregates(const ldu_amg *M, int level, int32_t *agg) {
     if (!M || !agg || level < 0 || level >= (int)M->lev.size())
         return LDU_ERR_BAD_ARG;
-    const auto &a = M->lev[(size_t)level].agg;
-    std::memcpy(agg, a.data(), sizeof(int32_t) * a.size());
-    return LDU_OK;
+    const amg_level &L = M->lev[(size_t)level];
+    const cudaError_t e =
+        cudaMemcpy(agg, L.agg, sizeof(int32_t) * (size_t)L.n, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
 }
 
 int ldu_amg_vcycle(ldu_amg *M, int precision, const void *b, void *x, ldu_stream_t stream) {

@@ -1,0 +1,592 @@
+// amg_setup.cuh -- device construction of the aggregation-AMG hierarchy
+// (Sec. 5; Table 2's AMG-CG, whose AMG the paper takes from CUSP, where the
+// aggregation forms a distance-2 maximal independent set in parallel: Bell,
+// Dalton & Olson, SIAM J. Sci. Comput. 34 (2012)).  Included by amg.cu.
+//
+// Every level is a CSR matrix on the device (rows with their diagonal,
+// columns sorted).  Per level:
+//   1. d = diag(A), rho = max_i sum_j |a_ij| / a_ii, w = 4 / (3 rho);
+//   2. distance-2 MIS by rounds: every row holds (state, h_i), state 0
+//      excluded, 1 undecided, 2 root, h_i = mix64((i + 1) * golden) (the
+//      SplitMix64 output of counter i + 1, Steele, Lea & Flood 2014);
+//      two sweeps of "largest pair over the row and its neighbours" give the
+//      largest pair within distance 2; an undecided row whose largest pair is
+//      its own becomes a root, one whose largest pair is a root's is excluded;
+//   3. aggregates: roots numbered in row order; a row next to a root joins it;
+//      the others join the assigned neighbour of largest |a_ij| (ties within
+//      1e-12 of the row's largest |a_ij| go to the lower aggregate);
+//   4. P = (I - w D^-1 A) P_t on the structural pattern of (I + A) P_t;
+//   5. R = P^T; A P and A_c = R (A P), structural patterns (entries that
+//      cancel are kept), each row's sums formed in a fixed order so the
+//      result is the same on every run.
+// Sparse products expand each output row's candidate entries into a hash
+// table of its own (open addressing in a device scratch sized by an upper
+// bound of the row's entries), one thread per row adding them in expansion
+// order; the occupied entries are then sorted by column and packed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace amgs {
+
+constexpr int kT = 256;   // threads per block of the setup kernels
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+// the SplitMix64 finaliser (Steele, Lea & Flood 2014)
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+__device__ __forceinline__ uint64_t prio(int64_t i) { return mix64((uint64_t)(i + 1) * kGolden); }
+
+inline int blocks(int64_t work) {
+    const int64_t b = (work + kT - 1) / kT;
+    return (int)(b < 1 ? 1 : (b > (1 << 30) ? (1 << 30) : b));
+}
+
+// ---- exclusive scan of int64 values (three passes, recursive over block sums)
+
+constexpr int kScanItems = 1024;   // items per block: 256 threads x 4
+
+// block-local exclusive scan of items [0, m) (in[] read as 0 at and past n);
+// bsum[b] = the block's total
+__global__ void k_scan_block(const int64_t *in, int64_t n, int64_t m, int64_t *out,
+                             int64_t *bsum) {
+    __shared__ int64_t sm[kT];
+    const int64_t base = (int64_t)blockIdx.x * kScanItems + 4 * threadIdx.x;
+    int64_t v[4], t = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        t += v[k];
+    }
+    sm[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 1; o < kT; o <<= 1) {   // inclusive scan of the thread totals
+        const int64_t a = threadIdx.x >= (unsigned)o ? sm[threadIdx.x - o] : 0;
+        __syncthreads();
+        sm[threadIdx.x] += a;
+        __syncthreads();
+    }
+    int64_t run = sm[threadIdx.x] - t;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < m)
+            out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == kT - 1)
+        bsum[blockIdx.x] = sm[kT - 1];
+}
+
+__global__ void k_scan_add(int64_t *out, const int64_t *boff, int64_t m) {
+    const int64_t add = boff[blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kScanItems + threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int64_t j = base + (int64_t)k * kT;
+        if (j < m)
+            out[j] += add;
+    }
+}
+
+// scratch items scan_excl needs for n inputs
+inline int64_t scan_tmp_items(int64_t n) {
+    const int64_t nb = (n + 1 + kScanItems - 1) / kScanItems;
+    return nb > 1 ? 2 * nb + 1 + scan_tmp_items(nb) : nb;
+}
+
+// out[i] = in[0] + ... + in[i - 1] for i = 0..n (out[n] is the total); in
+// and out must not alias; tmp holds scan_tmp_items(n) items
+inline void scan_excl(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp,
+                      cudaStream_t st) {
+    const int64_t m = n + 1;
+    const int64_t nb = (m + kScanItems - 1) / kScanItems;
+    int64_t *bsum = tmp;
+    k_scan_block<<<(unsigned)nb, kT, 0, st>>>(in, n, m, out, bsum);
+    if (nb > 1) {
+        int64_t *boff = tmp + nb;   // nb + 1 entries
+        scan_excl(bsum, boff, nb, boff + nb + 1, st);
+        k_scan_add<<<(unsigned)nb, kT, 0, st>>>(out, boff, m);
+    }
+}
+
+// ---- the level-0 CSR from LDU faces -------------------------------------
+
+__global__ void k_ldu_len(int64_t nf, const int32_t *own, const int32_t *nbr, int64_t *len) {
+    const int64_t f = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (f < nf) {
+        atomicAdd((unsigned long long *)&len[own[f]], 1ull);
+        atomicAdd((unsigned long long *)&len[nbr[f]], 1ull);
+    }
+}
+
+__global__ void k_ones(int64_t n, int64_t *len) {
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (i < n)
+        len[i] = 1;
+}
+
+// entry slots of the expanded rows: (column, value, order key); the diagonal
+// first, then each face's two entries at atomically claimed slots (their
+// order key is the face number, so the sort below restores face order)
+__global__ void k_ldu_fill_diag(int64_t n, const int64_t *ptr, const double *diag, int *col,
+                                double *val, int64_t *key, int64_t *cur) {
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (i < n) {
+        const int64_t at = ptr[i];
+        col[at] = (int)i;
+        val[at] = diag[i];
+        key[at] = -1;
+        cur[i] = at + 1;
+    }
+}
+
+__global__ void k_ldu_fill_faces(int64_t nf, const int32_t *own, const int32_t *nbr,
+                                 const double *up, const double *lo, int *col, double *val,
+                                 int64_t *key, int64_t *cur) {
+    const int64_t f = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (f < nf) {
+        const int o = own[f], b = nbr[f];
+        const int64_t a1 = (int64_t)atomicAdd((unsigned long long *)&cur[o], 1ull);
+        col[a1] = b;
+        val[a1] = up[f];
+        key[a1] = f;
+        const int64_t a2 = (int64_t)atomicAdd((unsigned long long *)&cur[b], 1ull);
+        col[a2] = o;
+        val[a2] = lo[f];
+        key[a2] = f;
+    }
+}
+
+// sort each row's entries by (column, key) in place (insertion sort: rows
+// of a mesh are short), add entries of equal column in key order, and
+// write the number of distinct columns to cnt[i]; the merged entries are
+// left at the front of the row
+__global__ void k_row_sort_merge(int64_t n, const int64_t *ptr, int *col, double *val,
+                                 int64_t *key, int64_t *cnt) {
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    const int64_t b = ptr[i], e = ptr[i + 1];
+    for (int64_t k = b + 1; k < e; ++k) {
+        const int c = col[k];
+        const double v = val[k];
+        const int64_t q = key[k];
+        int64_t j = k - 1;
+        while (j >= b && (col[j] > c || (col[j] == c && key[j] > q))) {
+            col[j + 1] = col[j];
+            val[j + 1] = val[j];
+            key[j + 1] = key[j];
+            --j;
+        }
+        col[j + 1] = c;
+        val[j + 1] = v;
+        key[j + 1] = q;
+    }
+    int64_t w = b;
+    for (int64_t k = b; k < e; ++k) {
+        if (k > b && col[k] == col[w - 1]) {
+            val[w - 1] += val[k];
+            continue;
+        }
+        col[w] = col[k];
+        val[w] = val[k];
+        ++w;
+    }
+    cnt[i] = w - b;
+}
+
+// copy the first cnt entries of every expanded row into the packed CSR
+__global__ void k_pack(int64_t n, const int64_t *xptr, const int *xcol, const double *xval,
+                       const int64_t *ptr, int *col, double *val) {
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    const int64_t s = xptr[i];
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        col[k] = xcol[s + (k - ptr[i])];
+        val[k] = xval[s + (k - ptr[i])];
+    }
+}
+
+// ---- per-level scalars and the independent set --------------------------
+
+// d_i and max_i sum_j |a_ij| / a_ii (non-negative doubles order as their bits);
+// flags |= 1 when a diagonal is missing, non-positive or not finite
+__global__ void k_diag_rho(int n, const int64_t *ptr, const int *col, const double *val, double *d,
+                           unsigned long long *rho_bits, int *flags) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    double di = 0.0, s = 0.0;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        s += fabs(val[k]);
+        if (col[k] == i)
+            di = val[k];
+    }
+    d[i] = di;
+    if (!(di > 0.0) || !isfinite(di) || !isfinite(s)) {
+        atomicOr(flags, 1);
+        return;
+    }
+    const double r = s / di;
+    atomicMax(rho_bits, (unsigned long long)__double_as_longlong(r));
+}
+
+__device__ __forceinline__ bool pair_less(int sa, uint64_t ha, int sb, uint64_t hb) {
+    return sa < sb || (sa == sb && ha < hb);
+}
+
+// the largest (state, h) over row i and its neighbours
+__global__ void k_pair_max(int n, const int64_t *ptr, const int *col, const int *s_in,
+                           const uint64_t *h_in, int *s_out, uint64_t *h_out) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    int bs = s_in[i];
+    uint64_t bh = h_in[i];
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const int j = col[k];
+        const int sj = s_in[j];
+        const uint64_t hj = h_in[j];
+        if (pair_less(bs, bh, sj, hj)) {
+            bs = sj;
+            bh = hj;
+        }
+    }
+    s_out[i] = bs;
+    h_out[i] = bh;
+}
+
+__global__ void k_mis_init(int n, int *state, uint64_t *h) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i < n) {
+        state[i] = 1;
+        h[i] = prio(i);
+    }
+}
+
+// one round's decisions; *left counts rows still undecided afterwards
+__global__ void k_mis_update(int n, int *state, const uint64_t *h, const int *s2,
+                             const uint64_t *h2, unsigned *left) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    if (state[i] != 1)
+        return;
+    if (s2[i] == 1 && h2[i] == h[i]) {
+        state[i] = 2;
+    } else if (s2[i] == 2) {
+        state[i] = 0;
+    } else {
+        atomicAdd(left, 1u);
+    }
+}
+
+__global__ void k_root_flags(int n, const int *state, int64_t *flag) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i < n)
+        flag[i] = state[i] == 2 ? 1 : 0;
+}
+
+// roots: their number; other rows: the root they are next to, else -1
+__global__ void k_agg_roots(int n, const int64_t *ptr, const int *col, const int *state,
+                            const int64_t *rank, int *first) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    if (state[i] == 2) {
+        first[i] = (int)rank[i];
+        return;
+    }
+    int a = -1;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const int j = col[k];
+        if (j != i && state[j] == 2)
+            a = (int)rank[j];
+    }
+    first[i] = a;
+}
+
+// rows not yet assigned: the assigned neighbour of largest |a_ij|, ties
+// within TIE of the row's largest |a_ij| going to the lower aggregate;
+// flags |= 2 when a row has no assigned neighbour
+__global__ void k_agg_rest(int n, const int64_t *ptr, const int *col, const double *val,
+                           const int *first, int *agg, double tie, int *flags) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    if (first[i] >= 0) {
+        agg[i] = first[i];
+        return;
+    }
+    double mx = 0.0;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k)
+        if (col[k] != i)
+            mx = fmax(mx, fabs(val[k]));
+    const double tol = tie * mx;
+    int best = -1;
+    double best_v = -1.0;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const int j = col[k];
+        if (j == i || first[j] < 0)
+            continue;
+        const double a = fabs(val[k]);
+        if (best < 0 || a > best_v + tol) {
+            best = first[j];
+            best_v = a;
+        } else if (a >= best_v - tol && first[j] < best) {
+            best = first[j];
+            best_v = fmax(a, best_v);
+        }
+    }
+    if (best < 0)
+        atomicOr(flags, 2);
+    agg[i] = best < 0 ? 0 : best;
+}
+
+// ---- prolongator ----------------------------------------------------------
+
+// expand row i of P: (agg(j), a_ij) for every stored entry of row i of A, in
+// A's slot order (the key), into the row's own slots of the expansion
+__global__ void k_p_expand(int n, const int64_t *ptr, const int *col, const double *val,
+                           const int *agg, int *xcol, double *xval, int64_t *xkey) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        xcol[k] = agg[col[k]];
+        xval[k] = val[k];
+        xkey[k] = k;
+    }
+}
+
+// the merged row of D^-1 A P_t into P's values: [J == agg(i)] - w/d_i sum
+__global__ void k_p_values(int n, const int64_t *xptr, const int64_t *cnt, int *xcol,
+                           double *xval, const int *agg, const double *d, double w) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    const double s = w / d[i];
+    const int own = agg[i];
+    for (int64_t k = xptr[i]; k < xptr[i] + cnt[i]; ++k)
+        xval[k] = (xcol[k] == own ? 1.0 : 0.0) - s * xval[k];
+}
+
+// ---- transpose --------------------------------------------------------------
+
+__global__ void k_col_count(int64_t nnz, const int *col, int64_t *len) {
+    const int64_t k = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (k < nnz)
+        atomicAdd((unsigned long long *)&len[col[k]], 1ull);
+}
+
+__global__ void k_transpose_fill(int n, const int64_t *ptr, const int *col, const double *val,
+                                 int64_t *cur, int *tcol, double *tval, int64_t *tkey) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+        const int64_t at = (int64_t)atomicAdd((unsigned long long *)&cur[col[k]], 1ull);
+        tcol[at] = i;
+        tval[at] = val[k];
+        tkey[at] = 0;
+    }
+}
+
+__global__ void k_copy_i64(int64_t n, const int64_t *a, int64_t *b) {
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (i < n)
+        b[i] = a[i];
+}
+
+// ---- sparse product C = X Y (structural pattern, fixed summation order) ----
+
+// upper bound of row i's entries: sum over X's row of the lengths of Y's rows
+__global__ void k_gemm_bound(int n, const int64_t *xp, const int *xc, const int64_t *yp,
+                             int64_t *ub) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    int64_t t = 0;
+    for (int64_t k = xp[i]; k < xp[i + 1]; ++k)
+        t += yp[xc[k] + 1] - yp[xc[k]];
+    ub[i] = t;
+}
+
+// table size of row i: the smallest power of two above ub (0 for an empty
+// row), so that a probe always finds a free slot; the distinct columns of a
+// row are far fewer than ub, so the table stays sparse
+__global__ void k_gemm_tsize(int n, const int64_t *ub, int64_t *ts) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    int64_t s = 0;
+    if (ub[i] > 0) {
+        s = 2;
+        while (s <= ub[i])
+            s <<= 1;
+    }
+    ts[i] = s;
+}
+
+__device__ __forceinline__ uint32_t slot_hash(int c) { return (uint32_t)c * 2654435761u; }
+
+// row i of C: every x_ik y_kj added into the row's own hash table in the
+// order (k, j) of the two rows; the occupied slots then sorted by column
+// into the front of the table and their number written to cnt[i]
+__global__ void k_gemm_rows(int n, const int64_t *xp, const int *xc, const double *xv,
+                            const int64_t *yp, const int *yc, const double *yv,
+                            const int64_t *tp, int *tcol, double *tval, int64_t *cnt) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    const int64_t base = tp[i], size = tp[i + 1] - base;
+    int *tc = tcol + base;
+    double *tv = tval + base;
+    for (int64_t s = 0; s < size; ++s)
+        tc[s] = -1;
+    const uint64_t mask = (uint64_t)size - 1;
+    int64_t used = 0;
+    for (int64_t k = xp[i]; k < xp[i + 1]; ++k) {
+        const int r = xc[k];
+        const double a = xv[k];
+        for (int64_t q = yp[r]; q < yp[r + 1]; ++q) {
+            const int c = yc[q];
+            uint64_t h = slot_hash(c) & mask;
+            while (tc[h] != -1 && tc[h] != c)
+                h = (h + 1) & mask;
+            if (tc[h] == -1) {
+                tc[h] = c;
+                tv[h] = a * yv[q];
+                ++used;
+            } else {
+                tv[h] += a * yv[q];
+            }
+        }
+    }
+    // pack the occupied slots to the front, then sort them by column
+    int64_t w = 0;
+    for (int64_t s = 0; s < size; ++s)
+        if (tc[s] != -1) {
+            tc[w] = tc[s];
+            tv[w] = tv[s];
+            ++w;
+        }
+    for (int64_t k = 1; k < w; ++k) {
+        const int c = tc[k];
+        const double v = tv[k];
+        int64_t j = k - 1;
+        while (j >= 0 && tc[j] > c) {
+            tc[j + 1] = tc[j];
+            tv[j + 1] = tv[j];
+            --j;
+        }
+        tc[j + 1] = c;
+        tv[j + 1] = v;
+    }
+    cnt[i] = used;
+}
+
+// ---- the level's device layouts --------------------------------------------
+
+__global__ void k_offdiag_len(int n, const int64_t *ptr, const int *col, int64_t *len) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    int64_t t = 0;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k)
+        t += col[k] != i;
+    len[i] = t;
+}
+
+// widest off-diagonal row of each 32-row slice
+__global__ void k_slice32_width(int n, const int64_t *len, int64_t *sw) {
+    const int s = blockIdx.x * kT + threadIdx.x;
+    if (s >= (n + 31) / 32)
+        return;
+    int64_t w = 0;
+    for (int r = s * 32; r < min(n, s * 32 + 32); ++r)
+        w = max(w, len[r]);
+    sw[s] = w;
+}
+
+__global__ void k_slice32_slots(int ns, const int64_t *sw, int64_t *slots) {
+    const int s = blockIdx.x * kT + threadIdx.x;
+    if (s < ns)
+        slots[s] = 32 * sw[s];
+}
+
+// A's off-diagonal part in 32-row sliced ELL (padding: column 0, value 0;
+// 16-bit offsets: 0, the row itself) and whether every offset fits 16 bits
+__global__ void k_sell32_fill(int n, const int64_t *ptr, const int *col, const double *val,
+                              const int64_t *sp, const int64_t *sw, int *scol, double *sval,
+                              short *c16, int *flags) {
+    const int row = blockIdx.x * kT + threadIdx.x;
+    if (row >= (n + 31) / 32 * 32)
+        return;
+    const int s = row >> 5, i = row & 31;
+    int k = 0;
+    if (row < n)
+        for (int64_t e = ptr[row]; e < ptr[row + 1]; ++e) {
+            const int c = col[e];
+            if (c == row)
+                continue;
+            const int64_t at = sp[s] + (int64_t)k * 32 + i;
+            scol[at] = c;
+            sval[at] = val[e];
+            const int off = c - row;
+            if (off < -32768 || off > 32767)
+                atomicOr(flags, 4);
+            c16[at] = (short)off;
+            ++k;
+        }
+    for (; k < sw[s]; ++k) {
+        const int64_t at = sp[s] + (int64_t)k * 32 + i;
+        scol[at] = 0;
+        sval[at] = 0.0;
+        c16[at] = 0;
+    }
+}
+
+// A's off-diagonal part in CSR (int32 row pointers)
+__global__ void k_offdiag_csr(int n, const int64_t *ptr, const int *col, const double *val,
+                              const int64_t *optr, int *oc, double *ov) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i >= n)
+        return;
+    int64_t w = optr[i];
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k)
+        if (col[k] != i) {
+            oc[w] = col[k];
+            ov[w] = val[k];
+            ++w;
+        }
+}
+
+__global__ void k_i64_to_i32(int64_t n, const int64_t *a, int *b) {
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (i < n)
+        b[i] = (int)a[i];
+}
+
+__global__ void k_d2f(int64_t n, const double *a, float *b) {
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (i < n)
+        b[i] = (float)a[i];
+}
+
+__global__ void k_wd(int n, const double *d, double w, double *wd) {
+    const int i = blockIdx.x * kT + threadIdx.x;
+    if (i < n)
+        wd[i] = w / d[i];
+}
+
+}  // namespace amgs

@@ -18,12 +18,73 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def test_chain_aggregates_by_hand():
-    """1 x 1 x 9 chain: roots 0, 3, 6 take their neighbours ({0,1}, {2,3,4},
-    {5,6,7}); row 8 has only the aggregated 7 and joins its aggregate."""
+    """1 x 1 x 9 chain.  The priorities h_i = mix64((i + 1) golden) of rows
+    0..8 rank 3 > 0 > 7 > 1 > 5 > 8 > 6 > 4 > 2.  Round 1: row 3 is the
+    largest within distance 2 of itself (rows 1..5), so are row 0 (rows
+    0..2) and row 7 (rows 5..8); every other row sees one of them, so none of
+    the rest is a local maximum.  Round 2: every remaining row has a root
+    within two steps and is excluded.  Roots 0, 3, 7 number the aggregates
+    0, 1, 2; rows 1, 2, 4, 6, 8 sit next to a root and join it; row 5 sees
+    aggregate 1 (row 4) and aggregate 2 (row 6) with equal strength and takes
+    the lower."""
     s = lc.poisson_box(9, 1, 1)
+    h = amg.priorities(9)
+    assert np.argsort(-h.astype(np.float64)).tolist() == [3, 0, 7, 1, 5, 8, 6, 4, 2]
+    roots, rounds = amg.mis2(amg.csr_of(s))
+    assert np.flatnonzero(roots).tolist() == [0, 3, 7] and rounds == 2
     agg, na = amg.aggregate(amg.csr_of(s))
     assert na == 3
-    assert agg.tolist() == [0, 0, 1, 1, 1, 2, 2, 2, 2]
+    assert agg.tolist() == [0, 0, 1, 1, 1, 1, 2, 2, 2]
+
+
+def _distances(A, src):
+    """Graph distances from src over the off-diagonal pattern (BFS)."""
+    n = A.shape[0]
+    dist = np.full(n, -1)
+    dist[src] = 0
+    todo = deque([src])
+    while todo:
+        u = todo.popleft()
+        for v in A.indices[A.indptr[u]:A.indptr[u + 1]]:
+            if dist[v] < 0:
+                dist[v] = dist[u] + 1
+                todo.append(v)
+    return dist
+
+
+@pytest.mark.parametrize("make", [lambda: lc.poisson_box(6, 5, 4, diffusivity="lognormal", seed=2),
+                                  lambda: lc.config2(s=7), lambda: lc.config3(s=6)])
+def test_mis2_is_independent_maximal_and_starts_from_local_maxima(make):
+    """Brute force on small graphs: no two roots within distance 2, every
+    other row within distance 2 of a root, and every row that holds the
+    largest priority of its distance-2 neighbourhood is a root (those are
+    exactly the first round's roots, which no later round can exclude)."""
+    A = amg.csr_of(make())
+    roots, _ = amg.mis2(A)
+    h = amg.priorities(A.shape[0])
+    for i in range(A.shape[0]):
+        dist = _distances(A, i)
+        near = np.flatnonzero((dist >= 0) & (dist <= 2))
+        if roots[i]:
+            assert not np.any(roots[near[near != i]])
+        else:
+            assert np.any(roots[near])
+        if h[i] == h[near].max():
+            assert roots[i]
+
+
+def test_coarse_patterns_are_structural():
+    """A coarse entry that cancels to zero stays in the pattern: the
+    Galerkin pattern is the product of the patterns, whatever the values."""
+    s = lc.poisson_box(6, 6, 6)
+    A = amg.csr_of(s)
+    agg, na = amg.aggregate(A)
+    P = amg.prolongator(A, agg, na, amg.jacobi_weight(A))
+    Ac = amg.galerkin(A, P)
+    pat = amg.pattern_of(P).T @ amg.pattern_of(A) @ amg.pattern_of(P)
+    assert Ac.nnz == sp.csr_matrix(pat).nnz
+    dense = P.T.toarray() @ A.toarray() @ P.toarray()
+    assert np.allclose(Ac.toarray(), dense, rtol=1e-13, atol=1e-15 * abs(dense).max())
 
 
 def test_isolated_rows_are_singletons():
