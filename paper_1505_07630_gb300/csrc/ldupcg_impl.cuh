@@ -680,6 +680,47 @@ __device__ __forceinline__ uint64_t l2_evict_first_policy() {
     return pol;
 }
 
+// An L2 policy that marks lines evict-last: the float vectors of the mixed
+// sweep (about 59 MB at 128^3) are read and written every iteration and
+// should stay in the 129 MB L2 while the matrix streams past them.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// R consecutive floats with an L2 cache policy (load and store)
+template <int R>
+__device__ __forceinline__ void ld_rows_pol(const float *p, float (&o)[R], uint64_t pol) {
+    if constexpr (R == 4) {
+        asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3])
+                     : "l"(p), "l"(pol));
+    } else if constexpr (R == 2) {
+        asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+                     : "=f"(o[0]), "=f"(o[1])
+                     : "l"(p), "l"(pol));
+    } else {
+        asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(o[0]) : "l"(p), "l"(pol));
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void st_rows_pol(float *p, const float (&o)[R], uint64_t pol) {
+    if constexpr (R == 4) {
+        asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
+                     "f"(o[0]), "f"(o[1]), "f"(o[2]), "f"(o[3]), "l"(pol)
+                     : "memory");
+    } else if constexpr (R == 2) {
+        asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(o[0]),
+                     "f"(o[1]), "l"(pol)
+                     : "memory");
+    } else {
+        asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(o[0]), "l"(pol)
+                     : "memory");
+    }
+}
+
 // bytes from global src to shared dst, completing on bar (both 16-byte
 // aligned, bytes a multiple of 16), with L2 policy pol
 __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes,

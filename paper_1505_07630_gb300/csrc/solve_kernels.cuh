@@ -1090,10 +1090,13 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
         bool staged_ok = true;
         if constexpr (STG)
             pipe_begin(A, pipe, range, warp, nwarps, lane);
+        // the vectors' own rows are read and written with an evict-last L2
+        // policy (measured 3 % faster at 128^3 than default caching)
+        const uint64_t vpol = l2_evict_last_policy();
         FOR_MY_SLICES(s) {
             const int row0 = s * A.C + R * lane;
             float nn[R], ww[R];
-            ld_rows<R>(w + row0, ww);
+            ld_rows_pol<R>(w + row0, ww, vpol);
 #pragma unroll
             for (int j = 0; j < R; ++j)
                 nn[j] = ww[j];
@@ -1105,11 +1108,11 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
             float zz[R], ss[R], pp[R], xx[R], rr[R];
             float dw[R], dq[R], dt[R];
             auto load_rows = [&]() {
-                ld_rows<R>(z + row0, zz);
-                ld_rows<R>(sv + row0, ss);
-                ld_rows<R>(p + row0, pp);
-                ld_rows<R>(xc + row0, xx);
-                ld_rows<R>(r + row0, rr);
+                ld_rows_pol<R>(z + row0, zz, vpol);
+                ld_rows_pol<R>(sv + row0, ss, vpol);
+                ld_rows_pol<R>(p + row0, pp, vpol);
+                ld_rows_pol<R>(xc + row0, xx, vpol);
+                ld_rows_pol<R>(r + row0, rr, vpol);
                 if (defl) {
                     ld_rows<R>(w0f + row0, dw);
                     ld_rows<R>(q0f + row0, dq);
@@ -1168,12 +1171,12 @@ __device__ __forceinline__ bool mixed_body(const SolveParams &P, const Scope &sc
             g0.add(e0);
             g1.add(e1);
             g2.add(e2);
-            st_rows<R>(z + row0, zz);
-            st_rows<R>(sv + row0, ss);
-            st_rows<R>(p + row0, pp);
-            st_rows<R>(xc + row0, xx);
-            st_rows<R>(r + row0, rr);
-            st_rows<R>(wn + row0, ww);
+            st_rows_pol<R>(z + row0, zz, vpol);
+            st_rows_pol<R>(sv + row0, ss, vpol);
+            st_rows_pol<R>(p + row0, pp, vpol);
+            st_rows_pol<R>(xc + row0, xx, vpol);
+            st_rows_pol<R>(r + row0, rr, vpol);
+            st_rows_pol<R>(wn + row0, ww, vpol);
         }
         if constexpr (STG) {
             if (!staged_ok) {
