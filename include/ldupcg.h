@@ -113,7 +113,9 @@ typedef struct ldu_solve_stats {
     int status;
     int iters;              /* A*p products of the loop (float ones for LDU_MIXED) */
     int replacements;       /* true-residual evaluations, initial one included */
-    double relres;          /* ||b - A x||_2 / ||b||_2 at exit, in FP64 */
+    double relres;          /* ||b - A x||_2 / ||b||_2 at exit: the residual formed
+                               in FP64 (LDU_MIXED: its norm summed from its float
+                               rounding, relative accuracy about 1e-7) */
     double bnorm;           /* ||b||_2 */
     int grid_blocks;        /* blocks of the persistent launch */
     int block_threads;
@@ -197,7 +199,9 @@ int pcg_solve(const ldu_matrix *A, const double *b, double *x, double tol, int m
  *              the recursive residual reaches tol (and every rr_period steps);
  *              LDU_MIXED: the recurrences in float on a float copy of the
  *              matrix; the solution accumulates in double and the residual
- *              is replaced by the double b - A x every rr_period steps and
+ *              is replaced by the double b - A x (its norms, for the
+ *              stopping test and relres, summed from its float rounding as
+ *              float pairs: relative accuracy about 1e-7) every rr_period steps and
  *              whenever (r, M^-1 r) has dropped by tau^2 (opts; by default
  *              every 16 steps or on a 0.3^2 drop).  Convergence is only
  *              declared on such a double residual.  deflate = 1 adds the
