@@ -1328,7 +1328,7 @@ int spgemm(Scratch &S, const GCsr &X, const GCsr &Y, GCsr &Z) {
     CKS(S.get(&ub, n));
     CKS(S.get(&ts, n));
     k_gemm_bound<<<blocks(n), kT, 0, S.st>>>(n, X.ptr, X.col, Y.ptr, ub);
-    k_gemm_tsize<<<blocks(n), kT, 0, S.st>>>(n, ub, ts);
+    k_gemm_tsize<<<blocks(n), kT, 0, S.st>>>(n, ub, Y.m, ts);
     LAUNCHED();
     if (int rc = exscan(S, ts, n, &tp, &tsize))
         return rc;

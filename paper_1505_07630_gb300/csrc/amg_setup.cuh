@@ -165,31 +165,66 @@ __global__ void k_ldu_fill_faces(int64_t nf, const int32_t *own, const int32_t *
     }
 }
 
-// sort each row's entries by (column, key) in place (insertion sort: rows
-// of a mesh are short), add entries of equal column in key order, and
-// write the number of distinct columns to cnt[i]; the merged entries are
-// left at the front of the row
+// In-place sort of m entries (column c, order key q, value v) by (c, q),
+// every (c, q) pair distinct, so the result does not depend on the method:
+// insertion sort for the short rows of a mesh, heapsort (m log m) for the
+// long rows of transposes and coarse levels.
+__device__ __forceinline__ bool entry_less(const int *c, const int64_t *q, int64_t a, int64_t b) {
+    return c[a] < c[b] || (c[a] == c[b] && (q ? q[a] < q[b] : false));
+}
+
+__device__ __forceinline__ void entry_swap(int *c, int64_t *q, double *v, int64_t a, int64_t b) {
+    const int tc = c[a];
+    c[a] = c[b];
+    c[b] = tc;
+    const double tv = v[a];
+    v[a] = v[b];
+    v[b] = tv;
+    if (q) {
+        const int64_t tq = q[a];
+        q[a] = q[b];
+        q[b] = tq;
+    }
+}
+
+__device__ void sort_entries(int *c, int64_t *q, double *v, int64_t m) {
+    if (m <= 32) {
+        for (int64_t k = 1; k < m; ++k)
+            for (int64_t j = k; j > 0 && entry_less(c, q, j, j - 1); --j)
+                entry_swap(c, q, v, j, j - 1);
+        return;
+    }
+    auto sift = [&](int64_t root, int64_t end) {   // max-heap on [0, end)
+        for (;;) {
+            int64_t child = 2 * root + 1;
+            if (child >= end)
+                return;
+            if (child + 1 < end && entry_less(c, q, child, child + 1))
+                ++child;
+            if (!entry_less(c, q, root, child))
+                return;
+            entry_swap(c, q, v, root, child);
+            root = child;
+        }
+    };
+    for (int64_t r = m / 2 - 1; r >= 0; --r)
+        sift(r, m);
+    for (int64_t end = m - 1; end > 0; --end) {
+        entry_swap(c, q, v, 0, end);
+        sift(0, end);
+    }
+}
+
+// sort each row's entries by (column, key) in place, add entries of equal
+// column in key order, and write the number of distinct columns to cnt[i];
+// the merged entries are left at the front of the row
 __global__ void k_row_sort_merge(int64_t n, const int64_t *ptr, int *col, double *val,
                                  int64_t *key, int64_t *cnt) {
     const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
     if (i >= n)
         return;
     const int64_t b = ptr[i], e = ptr[i + 1];
-    for (int64_t k = b + 1; k < e; ++k) {
-        const int c = col[k];
-        const double v = val[k];
-        const int64_t q = key[k];
-        int64_t j = k - 1;
-        while (j >= b && (col[j] > c || (col[j] == c && key[j] > q))) {
-            col[j + 1] = col[j];
-            val[j + 1] = val[j];
-            key[j + 1] = key[j];
-            --j;
-        }
-        col[j + 1] = c;
-        val[j + 1] = v;
-        key[j + 1] = q;
-    }
+    sort_entries(col + b, key + b, val + b, e - b);
     int64_t w = b;
     for (int64_t k = b; k < e; ++k) {
         if (k > b && col[k] == col[w - 1]) {
@@ -421,17 +456,18 @@ __global__ void k_gemm_bound(int n, const int64_t *xp, const int *xc, const int6
     ub[i] = t;
 }
 
-// table size of row i: the smallest power of two above ub (0 for an empty
-// row), so that a probe always finds a free slot; the distinct columns of a
-// row are far fewer than ub, so the table stays sparse
-__global__ void k_gemm_tsize(int n, const int64_t *ub, int64_t *ts) {
+// table size of row i: the smallest power of two above the row's possible
+// distinct columns, at most min(ub, m) with m the columns of the product
+// (0 for an empty row), so that a probe always finds a free slot
+__global__ void k_gemm_tsize(int n, const int64_t *ub, int64_t m, int64_t *ts) {
     const int i = blockIdx.x * kT + threadIdx.x;
     if (i >= n)
         return;
+    const int64_t d = ub[i] < m ? ub[i] : m;
     int64_t s = 0;
-    if (ub[i] > 0) {
+    if (d > 0) {
         s = 2;
-        while (s <= ub[i])
+        while (s <= d)
             s <<= 1;
     }
     ts[i] = s;
@@ -480,18 +516,7 @@ __global__ void k_gemm_rows(int n, const int64_t *xp, const int *xc, const doubl
             tv[w] = tv[s];
             ++w;
         }
-    for (int64_t k = 1; k < w; ++k) {
-        const int c = tc[k];
-        const double v = tv[k];
-        int64_t j = k - 1;
-        while (j >= 0 && tc[j] > c) {
-            tc[j + 1] = tc[j];
-            tv[j + 1] = tv[j];
-            --j;
-        }
-        tc[j + 1] = c;
-        tv[j + 1] = v;
-    }
+    sort_entries(tc, nullptr, tv, w);   // columns are distinct
     cnt[i] = used;
 }
 
