@@ -1318,7 +1318,34 @@ int ldu_to_csr(Scratch &S, int64_t n, int64_t nf, const int32_t *own, const int3
     return LDU_OK;
 }
 
-// Z = X Y on the structural pattern, each row summed in a fixed order
+// the rows of n whose len is at least thr: *list (device, *count entries)
+int long_rows(Scratch &S, const int64_t *len, int64_t n, int64_t thr, int **list, int64_t *count) {
+    using namespace amgs;
+    int64_t *flag, *rank;
+    CKS(S.get(&flag, n));
+    k_flag_long<<<blocks(n), kT, 0, S.st>>>(n, len, thr, flag);
+    LAUNCHED();
+    if (int rc = exscan(S, flag, n, &rank, count))
+        return rc;
+    CKS(S.get(list, *count));
+    if (*count > 0)
+        k_list_long<<<blocks(n), kT, 0, S.st>>>(n, flag, rank, *list);
+    LAUNCHED();
+    S.put(flag);
+    S.put(rank);
+    return LDU_OK;
+}
+
+__global__ void k_gather_i64(int64_t m, const int *list, const int64_t *a, int64_t *b) {
+    const int64_t k = (int64_t)blockIdx.x * amgs::kT + threadIdx.x;
+    if (k < m)
+        b[k] = a[list[k]];
+}
+
+// Z = X Y on the structural pattern, each row's sums independent of the
+// order of the threads that form them: a thread per row adding its products
+// in expansion order, or, for rows of many products, a block per row with
+// fixed-point integer sums
 int spgemm(Scratch &S, const GCsr &X, const GCsr &Y, GCsr &Z) {
     using namespace amgs;
     const int n = (int)X.n;
@@ -1335,9 +1362,32 @@ int spgemm(Scratch &S, const GCsr &X, const GCsr &Y, GCsr &Z) {
     CKS(S.get(&tcol, tsize));
     CKS(S.get(&tval, tsize));
     CKS(S.get(&cnt, n));
-    k_gemm_rows<<<blocks(n), kT, 0, S.st>>>(n, X.ptr, X.col, X.val, Y.ptr, Y.col, Y.val, tp, tcol,
-                                            tval, cnt);
+    k_gemm_rows<<<blocks(n), kT, 0, S.st>>>(n, X.ptr, X.col, X.val, Y.ptr, Y.col, Y.val, ub, tp,
+                                            tcol, tval, cnt);
     LAUNCHED();
+    {
+        int *list;
+        int64_t nlong = 0;
+        if (int rc = long_rows(S, ub, n, kLongRow, &list, &nlong))
+            return rc;
+        if (nlong > 0) {
+            int64_t *tsl, *lp, lsize = 0;
+            long long *fix;
+            CKS(S.get(&tsl, nlong));
+            k_gather_i64<<<blocks(nlong), kT, 0, S.st>>>(nlong, list, ts, tsl);
+            LAUNCHED();
+            if (int rc = exscan(S, tsl, nlong, &lp, &lsize))
+                return rc;
+            CKS(S.get(&fix, 2 * lsize));
+            k_gemm_long_rows<<<(unsigned)nlong, kT, kSortSmem, S.st>>>(
+                list, X.ptr, X.col, X.val, Y.ptr, Y.col, Y.val, ub, tp, lp, tcol, tval, fix, cnt);
+            LAUNCHED();
+            S.put(tsl);
+            S.put(lp);
+            S.put(fix);
+        }
+        S.put(list);
+    }
     Z.n = X.n;
     Z.m = Y.m;
     if (int rc = exscan(S, cnt, n, &Z.ptr, &Z.nnz))
@@ -1558,8 +1608,22 @@ int build_level(Scratch &S, const GCsr &A, bool first, int lanes, amg_level &L, 
         k_copy_i64<<<blocks(na), kT, 0, S.st>>>(na, R.ptr, cur);
         k_transpose_fill<<<blocks(n), kT, 0, S.st>>>(n, P.ptr, P.col, P.val, cur, R.col, R.val,
                                                       rkey);
-        k_row_sort_merge<<<blocks(na), kT, 0, S.st>>>(na, R.ptr, R.col, R.val, rkey, rlen);
+        // short rows by a thread each, long ones by a block each (the rows
+        // of a transpose hold distinct columns: sorting is all they need)
+        k_row_sort_merge<<<blocks(na), kT, 0, S.st>>>(na, R.ptr, R.col, R.val, rkey, rlen,
+                                                      kLongSort - 1);
         LAUNCHED();
+        {
+            int *list;
+            int64_t nlong = 0;
+            if (int rc = long_rows(S, rlen, na, kLongSort, &list, &nlong))
+                return rc;
+            if (nlong > 0)
+                k_sort_long_rows<<<(unsigned)nlong, kT, kSortSmem, S.st>>>(list, R.ptr, R.col,
+                                                                           R.val);
+            LAUNCHED();
+            S.put(list);
+        }
         for (const void *p : {(const void *)rlen, (const void *)cur, (const void *)rkey})
             S.put(p);
     }

@@ -28,9 +28,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
 namespace amgs {
 
 constexpr int kT = 256;   // threads per block of the setup kernels
+constexpr int64_t kLongRow = 2048;   // products of a row of C = X Y from which it takes a block
+constexpr int64_t kLongSort = 256;   // entries of a transpose's row from which it takes a block
+constexpr int kSortMax = 2048;       // largest row a block sorts in shared memory (24 KB)
+constexpr size_t kSortSmem = (size_t)kSortMax * (sizeof(int) + sizeof(double));
 constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 
 // the SplitMix64 finaliser (Steele, Lea & Flood 2014)
@@ -219,11 +225,13 @@ __device__ void sort_entries(int *c, int64_t *q, double *v, int64_t m) {
 // column in key order, and write the number of distinct columns to cnt[i];
 // the merged entries are left at the front of the row
 __global__ void k_row_sort_merge(int64_t n, const int64_t *ptr, int *col, double *val,
-                                 int64_t *key, int64_t *cnt) {
+                                 int64_t *key, int64_t *cnt, int64_t max_len = INT64_MAX) {
     const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
     if (i >= n)
         return;
     const int64_t b = ptr[i], e = ptr[i + 1];
+    if (e - b > max_len)
+        return;   // a long row: sorted by k_sort_long_rows (distinct keys, no merging)
     sort_entries(col + b, key + b, val + b, e - b);
     int64_t w = b;
     for (int64_t k = b; k < e; ++k) {
@@ -258,21 +266,27 @@ __global__ void k_pack(int64_t n, const int64_t *xptr, const int *xcol, const do
 __global__ void k_diag_rho(int n, const int64_t *ptr, const int *col, const double *val, double *d,
                            unsigned long long *rho_bits, int *flags) {
     const int i = blockIdx.x * kT + threadIdx.x;
-    if (i >= n)
-        return;
-    double di = 0.0, s = 0.0;
-    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
-        s += fabs(val[k]);
-        if (col[k] == i)
-            di = val[k];
+    unsigned long long rb = 0;   // bits of this row's ratio (0 for no row)
+    if (i < n) {
+        double di = 0.0, s = 0.0;
+        for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+            s += fabs(val[k]);
+            if (col[k] == i)
+                di = val[k];
+        }
+        d[i] = di;
+        if (!(di > 0.0) || !isfinite(di) || !isfinite(s))
+            atomicOr(flags, 1);
+        else
+            rb = (unsigned long long)__double_as_longlong(s / di);
     }
-    d[i] = di;
-    if (!(di > 0.0) || !isfinite(di) || !isfinite(s)) {
-        atomicOr(flags, 1);
-        return;
+    // the warp's largest first, then one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long t = __shfl_down_sync(0xffffffffu, rb, o);
+        rb = t > rb ? t : rb;
     }
-    const double r = s / di;
-    atomicMax(rho_bits, (unsigned long long)__double_as_longlong(r));
+    if ((threadIdx.x & 31) == 0 && rb != 0)
+        atomicMax(rho_bits, rb);
 }
 
 __device__ __forceinline__ bool pair_less(int sa, uint64_t ha, int sb, uint64_t hb) {
@@ -480,10 +494,13 @@ __device__ __forceinline__ uint32_t slot_hash(int c) { return (uint32_t)c * 2654
 // into the front of the table and their number written to cnt[i]
 __global__ void k_gemm_rows(int n, const int64_t *xp, const int *xc, const double *xv,
                             const int64_t *yp, const int *yc, const double *yv,
-                            const int64_t *tp, int *tcol, double *tval, int64_t *cnt) {
+                            const int64_t *ub, const int64_t *tp, int *tcol, double *tval,
+                            int64_t *cnt) {
     const int i = blockIdx.x * kT + threadIdx.x;
     if (i >= n)
         return;
+    if (ub[i] >= kLongRow)
+        return;   // k_gemm_long_rows forms this row
     const int64_t base = tp[i], size = tp[i + 1] - base;
     int *tc = tcol + base;
     double *tv = tval + base;
@@ -518,6 +535,191 @@ __global__ void k_gemm_rows(int n, const int64_t *xp, const int *xc, const doubl
         }
     sort_entries(tc, nullptr, tv, w);   // columns are distinct
     cnt[i] = used;
+}
+
+// ---- long rows: a block per row -----------------------------------------------
+//
+// Rows with many entries (the transposes and products of the coarse levels:
+// thousands of entries in a few thousand rows) take a block of kT threads
+// each instead of one thread.
+
+
+__global__ void k_flag_long(int64_t n, const int64_t *len, int64_t thr, int64_t *flag) {
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (i < n)
+        flag[i] = len[i] >= thr ? 1 : 0;
+}
+
+// list[rank[i]] = i for the flagged rows (rank: the exclusive scan of flag)
+__global__ void k_list_long(int64_t n, const int64_t *flag, const int64_t *rank, int *list) {
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
+    if (i < n && flag[i])
+        list[rank[i]] = (int)i;
+}
+
+// the block's bitonic sort of m <= kSortMax (column, value) pairs with
+// distinct columns, in place in global memory, through shared memory
+__device__ void block_sort_pairs(int *col, double *val, int m) {
+    extern __shared__ __align__(16) unsigned char sort_smem[];
+    int *sc = reinterpret_cast<int *>(sort_smem);
+    double *sv = reinterpret_cast<double *>(sort_smem + sizeof(int) * kSortMax);
+    int p = 1;
+    while (p < m)
+        p <<= 1;
+    for (int t = threadIdx.x; t < p; t += blockDim.x) {
+        sc[t] = t < m ? col[t] : INT_MAX;
+        sv[t] = t < m ? val[t] : 0.0;
+    }
+    __syncthreads();
+    for (int k = 2; k <= p; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < p; t += blockDim.x) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const bool up = (t & k) == 0;
+                    if ((sc[t] > sc[u]) == up) {
+                        const int c = sc[t];
+                        sc[t] = sc[u];
+                        sc[u] = c;
+                        const double v = sv[t];
+                        sv[t] = sv[u];
+                        sv[u] = v;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        col[t] = sc[t];
+        val[t] = sv[t];
+    }
+    __syncthreads();
+}
+
+// sort the long rows of a CSR (distinct columns) by column, a block per row
+__global__ void k_sort_long_rows(const int *list, const int64_t *ptr, int *col, double *val) {
+    const int i = list[blockIdx.x];
+    const int64_t b = ptr[i], m = ptr[i + 1] - b;
+    if (m <= kSortMax) {
+        block_sort_pairs(col + b, val + b, (int)m);
+    } else if (threadIdx.x == 0) {
+        sort_entries(col + b, nullptr, val + b, m);
+    }
+}
+
+__device__ __forceinline__ double block_max(double v) {
+    __shared__ double red[kT / 32];
+    for (int o = 16; o > 0; o >>= 1)
+        v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        m = fmax(m, red[w]);
+    __syncthreads();
+    return m;
+}
+
+// Row i of C = X Y for a long row, a block per row.  The products are added
+// in parallel, so that the result is the same whatever the order, each one
+// is split into two 64-bit fixed-point parts relative to the row's largest
+// product (about 90 significant bits in all, more than an FP64 sum keeps)
+// and the parts are summed with integer atomics, which are associative.
+// The occupied slots are then packed in slot order, converted back to
+// double and sorted by column.  hi, lo: the row's fixed-point scratch.
+__global__ void k_gemm_long_rows(const int *list, const int64_t *xp, const int *xc, const double *xv,
+                                 const int64_t *yp, const int *yc, const double *yv,
+                                 const int64_t *ub, const int64_t *tp, const int64_t *lp,
+                                 int *tcol, double *tval, long long *fix, int64_t *cnt) {
+    const int i = list[blockIdx.x];
+    const int64_t base = tp[i], size = tp[i + 1] - base;
+    int *tc = tcol + base;
+    double *tv = tval + base;
+    long long *hi = fix + 2 * lp[blockIdx.x];
+    long long *lo = hi + size;
+    for (int64_t s2 = threadIdx.x; s2 < size; s2 += blockDim.x) {
+        tc[s2] = -1;
+        hi[s2] = 0;
+        lo[s2] = 0;
+    }
+    // largest |product| of the row
+    double mx = 0.0;
+    for (int64_t k = xp[i] + threadIdx.x; k < xp[i + 1]; k += blockDim.x) {
+        const double a = fabs(xv[k]);
+        const int r = xc[k];
+        for (int64_t q = yp[r]; q < yp[r + 1]; ++q)
+            mx = fmax(mx, a * fabs(yv[q]));
+    }
+    mx = block_max(mx);   // ends with a barrier: the table is initialised
+    int L = 1;
+    while (((int64_t)1 << L) <= ub[i])
+        ++L;
+    // |p 2^s1| < 2^(61 - L): a sum of ub parts cannot overflow
+    const int s1 = mx > 0.0 ? 61 - L - (ilogb(mx) + 1) : 0;
+    const int s2s = 61 - L;
+    const uint64_t mask = (uint64_t)size - 1;
+    for (int64_t k = xp[i] + threadIdx.x; k < xp[i + 1]; k += blockDim.x) {
+        const double a = xv[k];
+        const int r = xc[k];
+        for (int64_t q = yp[r]; q < yp[r + 1]; ++q) {
+            const int c = yc[q];
+            const double sc = ldexp(a * yv[q], s1);
+            const long long hv = (long long)sc;                    // integer part (exact)
+            const long long lv = llrint(ldexp(sc - (double)hv, s2s));   // fraction, 61 - L bits
+            uint64_t h = slot_hash(c) & mask;
+            for (;;) {
+                const int t = atomicCAS(tc + h, -1, c);
+                if (t == -1 || t == c)
+                    break;
+                h = (h + 1) & mask;
+            }
+            atomicAdd(reinterpret_cast<unsigned long long *>(hi + h), (unsigned long long)hv);
+            atomicAdd(reinterpret_cast<unsigned long long *>(lo + h), (unsigned long long)lv);
+        }
+    }
+    __syncthreads();
+    // pack the occupied slots to the front in slot order, as doubles
+    __shared__ int s_total;
+    __shared__ int s_warp[kT / 32];
+    if (threadIdx.x == 0)
+        s_total = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < size; c0 += blockDim.x) {
+        const int64_t s3 = c0 + threadIdx.x;
+        const bool occ = s3 < size && tc[s3] != -1;
+        int cv = 0;
+        double vv = 0.0;
+        if (occ) {
+            cv = tc[s3];
+            vv = ldexp((double)hi[s3] + ldexp((double)lo[s3], -s2s), -s1);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, occ);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0)
+            s_warp[wid] = __popc(bal);
+        __syncthreads();   // every thread has read its slot before any is written
+        int off = s_total;
+        for (int w = 0; w < wid; ++w)
+            off += s_warp[w];
+        off += __popc(bal & ((1u << lane) - 1u));
+        if (occ) {
+            tc[off] = cv;
+            tv[off] = vv;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                s_total += s_warp[w];
+        __syncthreads();
+    }
+    const int used = s_total;
+    if (used <= kSortMax)
+        block_sort_pairs(tc, tv, used);
+    else if (threadIdx.x == 0)
+        sort_entries(tc, nullptr, tv, used);
+    if (threadIdx.x == 0)
+        cnt[i] = used;
 }
 
 // ---- the level's device layouts --------------------------------------------
