@@ -301,6 +301,15 @@ def test_full_size_hierarchy_matches_oracle(pkg, amg):
     for lev in range(len(levels)):
         agg_o, _ = amg.aggregate(levels[lev][0])
         assert np.array_equal(pkg.ldu_amg_aggregates(M, lev), agg_o), lev
+    # structural patterns: every level stores exactly the oracle's entries
+    last_A, last_P, _ = levels[-1]
+    assert M.info()["nnz"] == [L[0].nnz for L in levels] + [amg.galerkin(last_A, last_P).nnz]
+    # the coarse levels' values, formed here by block-per-row fixed-point sums
+    # for their long rows, through one FP64 cycle against the oracle's
+    b = np.random.default_rng(6).uniform(-1, 1, s.n)
+    x = pkg.ldu_amg_vcycle(M, dev(b)).cpu().numpy()
+    xo = amg.vcycle(levels, coarse, b)
+    assert np.max(np.abs(x - xo)) <= 1e-11 * np.max(np.abs(xo))
     M.close()
 
 
