@@ -109,6 +109,7 @@ struct ldu_matrix {
     int32_t *owner, *neighbour;
     // values
     double *val64, *sd, *isd, *dg;
+    float *sdf;                // (float)sd: the scaling factors of the float product
     float *val32;
     // work vectors
     double *v64[10];

@@ -200,7 +200,7 @@ extern "C" int pcg_solve_ldu_noalloc(int64_t n, int64_t nFaces, const int32_t *o
                                                                      slice_ptr, cursor, col, fid);
     k_sort_rows<<<noalloc_blocks(n, 128), 128, 0, st>>>((int)n, C, slice_ptr, deg, col, fid);
     k_diag_scale<<<noalloc_blocks(n_pad, 256), 256, 0, st>>>((int)n, (int)n_pad, diag, sd, isd, dg,
-                                                              flags, nullptr);
+                                                              nullptr, flags, nullptr);
     k_values<<<noalloc_blocks(n_pad, 256), 256, 0, st>>>((int)n_pad, C, slice_ptr, slice_w, col,
                                                          fid, upper, lower, nullptr, sd, val64,
                                                          val32);

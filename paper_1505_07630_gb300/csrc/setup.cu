@@ -128,7 +128,7 @@ void free_handle(ldu_matrix *A) {
         return;
     ldu::free_batch(A);
     void *ptrs[] = {A->slice_ptr, A->slice_w, A->col, A->col16, A->fid, A->owner, A->neighbour,
-                    A->val64, A->sd, A->isd, A->dg, A->val32, A->slots, A->bar_count,
+                    A->val64, A->sd, A->isd, A->dg, A->sdf, A->val32, A->slots, A->bar_count,
                     A->bar_err, A->out_dev, A->flags_dev, A->row_cell, A->rhs};
     for (void *p : ptrs)
         if (p)
@@ -148,7 +148,8 @@ int values_from_arrays(ldu_matrix *A, const double *diag, const double *up, cons
                        cudaStream_t st) {
     const int T = 256;
     k_diag_scale<<<blocks_for(A->n_pad, T), T, 0, st>>>((int)A->n, (int)A->n_pad, diag, A->sd,
-                                                        A->isd, A->dg, A->flags_dev, A->row_cell);
+                                                        A->isd, A->dg, A->sdf, A->flags_dev,
+                                                        A->row_cell);
     k_values<<<blocks_for(A->n_pad, T), T, 0, st>>>((int)A->n_pad, A->C, A->slice_ptr, A->slice_w,
                                                     A->col, A->fid, up, lo, nullptr, A->sd,
                                                     A->val64, A->val32);
@@ -290,6 +291,7 @@ int ldu_create(int64_t n, int64_t nf, const int32_t *owner, const int32_t *neigh
     CK(dev_alloc(&A->sd, A->n_pad, &b));
     CK(dev_alloc(&A->isd, A->n_pad, &b));
     CK(dev_alloc(&A->dg, A->n_pad, &b));
+    CK(dev_alloc(&A->sdf, A->n_pad, &b));
     CK(dev_alloc(&A->owner, nf, &b));
     CK(dev_alloc(&A->neighbour, nf, &b));
     CK(dev_alloc(&cursor, std::max<int64_t>(n, 1), &b));
@@ -395,7 +397,7 @@ int ldu_set_face_coeffs(ldu_matrix *A, const double *coef, const double *diag_ex
     const int T = 256;
     k_diag_from_coef<<<blocks_for(A->n_pad, T), T, 0, st>>>(
         (int)A->n, (int)A->n_pad, A->C, A->slice_ptr, A->slice_w, A->fid, coef, diag_extra, A->sd,
-        A->isd, A->dg, A->flags_dev, A->row_cell);
+        A->isd, A->dg, A->sdf, A->flags_dev, A->row_cell);
     k_values<<<blocks_for(A->n_pad, T), T, 0, st>>>((int)A->n_pad, A->C, A->slice_ptr, A->slice_w,
                                                     A->col, A->fid, nullptr, nullptr, coef, A->sd,
                                                     A->val64, A->val32);
@@ -417,7 +419,7 @@ int ldu_spmv(const ldu_matrix *A, int precision, const void *x, void *y, ldu_str
                                                           (const double *)x, (double *)y);
     else if (precision == LDU_FP32)
         k_spmv<float><<<blocks_for(A->n, T), T, 0, st>>>((int)A->n, A->C, A->slice_ptr, A->slice_w,
-                                                         A->col, A->val32, A->sd,
+                                                         A->col, A->val32, A->sdf,
                                                          (const float *)x, (float *)y);
     else
         return LDU_ERR_BAD_ARG;

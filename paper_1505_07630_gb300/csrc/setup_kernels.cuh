@@ -143,7 +143,7 @@ __global__ void k_col16(int n_pad, int C, const int *slice_ptr, const int *slice
 // row map (batched handles) diag is in the caller's cell order and rows
 // between systems (map -1) keep a unit diagonal.
 __global__ void k_diag_scale(int n, int n_pad, const double *diag, double *sd, double *isd,
-                             double *dg, int *flags, const int *row_cell) {
+                             double *dg, float *sdf, int *flags, const int *row_cell) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad)
         return;
@@ -156,10 +156,14 @@ __global__ void k_diag_scale(int n, int n_pad, const double *diag, double *sd, d
         sd[r] = q;
         isd[r] = 1.0 / q;
         dg[r] = d;
+        if (sdf)
+            sdf[r] = (float)q;
     } else {
         sd[r] = 1.0;
         isd[r] = 1.0;
         dg[r] = 0.0;
+        if (sdf)
+            sdf[r] = 1.0f;
     }
 }
 
@@ -167,7 +171,7 @@ __global__ void k_diag_scale(int n, int n_pad, const double *diag, double *sd, d
 // (extra in the caller's cell order when a row map is given)
 __global__ void k_diag_from_coef(int n, int n_pad, int C, const int *slice_ptr, const int *slice_w,
                                  const uint32_t *fid, const double *coef, const double *extra,
-                                 double *sd, double *isd, double *dg, int *flags,
+                                 double *sd, double *isd, double *dg, float *sdf, int *flags,
                                  const int *row_cell) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_pad)
@@ -176,6 +180,7 @@ __global__ void k_diag_from_coef(int n, int n_pad, int C, const int *slice_ptr, 
         sd[r] = 1.0;
         isd[r] = 1.0;
         dg[r] = 0.0;
+        sdf[r] = 1.0f;
         return;
     }
     const int s = r / C, i = r - s * C;
@@ -193,6 +198,7 @@ __global__ void k_diag_from_coef(int n, int n_pad, int C, const int *slice_ptr, 
     sd[r] = q;
     isd[r] = 1.0 / q;
     dg[r] = d;
+    sdf[r] = (float)q;
 }
 
 // scaled off-diagonal values of every slot.  coef != nullptr: a = -coef[f];
@@ -220,23 +226,26 @@ __global__ void k_values(int n_pad, int C, const int *slice_ptr, const int *slic
     }
 }
 
-// y = A x = D^1/2 (I + Ahat_off) D^1/2 x, one thread per row (caller buffers
-// hold exactly n entries)
+// y = A x = D^1/2 (I + Ahat_off) D^1/2 x, one thread per row.  scale holds the
+// factors sd in the product's type: the float copy for the float product, so
+// that no entry converts a double (conversions run on this GPU's slow FP64
+// pipe, which they otherwise saturate).  Every column stored for a row below
+// n is below n (a padding slot points at its own row, with value 0), so the
+// loop needs no bounds test.  Caller buffers hold exactly n entries.
 template <typename T>
 __global__ void k_spmv(int n, int C, const int *slice_ptr, const int *slice_w, const int *col,
-                       const T *val, const double *sd, const T *__restrict__ x, T *__restrict__ y) {
+                       const T *val, const T *scale, const T *__restrict__ x, T *__restrict__ y) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n)
         return;
     const int s = r / C, i = r - s * C;
     const int w = slice_w[s];
-    const T sr = (T)sd[r];
+    const T sr = scale[r];
     T acc = sr * x[r];
     for (int k = 0; k < w; ++k) {
         const int at = slice_ptr[s] + k * C + i;
         const int c = col[at];
-        if (c < n)
-            acc = fma(val[at], (T)sd[c] * x[c], acc);
+        acc = fma(val[at], scale[c] * x[c], acc);
     }
     y[r] = sr * acc;
 }
