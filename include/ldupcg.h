@@ -26,7 +26,7 @@
  *    values are errors; no C++ exception crosses this interface.  On an
  *    error, outputs are unspecified but buffers stay valid.
  *  - A handle must not be used by two calls that may run concurrently: the
- *    solves of one handle share its work vectors.
+ *    solves and the double product of one handle share its work vectors.
  */
 #ifndef LDUPCG_H
 #define LDUPCG_H
@@ -172,9 +172,11 @@ int ldu_set_face_coeffs(ldu_matrix *A, const double *coef, const double *diag_ex
                         ldu_stream_t stream);
 
 /* y = A x (Sec. 2.1's sparse matrix-vector product; Table 1's first kernel).
- *   precision  LDU_FP64: x, y are device double[n], values in double;
+ *   precision  LDU_FP64: x, y are device double[n], values in double (two
+ *                        passes: D^1/2 x into a work vector of the handle,
+ *                        then the product);
  *              LDU_FP32: x, y are device float[n], values and sums in float.
- * Queued on stream. */
+ * x and y may not overlap.  Queued on stream. */
 int ldu_spmv(const ldu_matrix *A, int precision, const void *x, void *y, ldu_stream_t stream);
 
 /* Jacobi-preconditioned CG (Sec. 2, Eq. 9; Saad, Iterative Methods, Alg. 9.1

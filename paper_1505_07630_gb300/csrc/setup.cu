@@ -413,14 +413,19 @@ int ldu_spmv(const ldu_matrix *A, int precision, const void *x, void *y, ldu_str
         return LDU_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int T = 256;
-    if (precision == LDU_FP64)
-        k_spmv<double><<<blocks_for(A->n, T), T, 0, st>>>((int)A->n, A->C, A->slice_ptr, A->slice_w,
-                                                          A->col, A->val64, A->sd,
-                                                          (const double *)x, (double *)y);
-    else if (precision == LDU_FP32)
-        k_spmv<float><<<blocks_for(A->n, T), T, 0, st>>>((int)A->n, A->C, A->slice_ptr, A->slice_w,
-                                                         A->col, A->val32, A->sdf,
-                                                         (const float *)x, (float *)y);
+    if (precision == LDU_FP64) {
+        // two passes through a work vector: one FP64 operation per stored entry
+        double *u = A->v64[9];
+        k_spmv_prescale<double><<<blocks_for(A->n, T), T, 0, st>>>((int)A->n, A->sd,
+                                                                   (const double *)x, u);
+        k_spmv<double, true><<<blocks_for(A->n, T), T, 0, st>>>((int)A->n, A->C, A->slice_ptr,
+                                                                A->slice_w, A->col, A->val64, A->sd,
+                                                                u, (double *)y);
+    } else if (precision == LDU_FP32) {
+        k_spmv<float, false><<<blocks_for(A->n, T), T, 0, st>>>((int)A->n, A->C, A->slice_ptr,
+                                                                A->slice_w, A->col, A->val32, A->sdf,
+                                                                (const float *)x, (float *)y);
+    }
     else
         return LDU_ERR_BAD_ARG;
     return cuda_status(cudaGetLastError());

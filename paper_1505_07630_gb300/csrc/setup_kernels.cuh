@@ -229,10 +229,13 @@ __global__ void k_values(int n_pad, int C, const int *slice_ptr, const int *slic
 // y = A x = D^1/2 (I + Ahat_off) D^1/2 x, one thread per row.  scale holds the
 // factors sd in the product's type: the float copy for the float product, so
 // that no entry converts a double (conversions run on this GPU's slow FP64
-// pipe, which they otherwise saturate).  Every column stored for a row below
-// n is below n (a padding slot points at its own row, with value 0), so the
-// loop needs no bounds test.  Caller buffers hold exactly n entries.
-template <typename T>
+// pipe, which they otherwise saturate).  PRESCALED: x already holds u = sd x
+// (k_spmv_prescale), which leaves one FP64 operation per stored entry in the
+// double product instead of two; the products and their order are the same
+// either way.  Every column stored for a row below n is below n (a padding
+// slot points at its own row, with value 0), so the loop needs no bounds
+// test.  Caller buffers hold exactly n entries.
+template <typename T, bool PRESCALED>
 __global__ void k_spmv(int n, int C, const int *slice_ptr, const int *slice_w, const int *col,
                        const T *val, const T *scale, const T *__restrict__ x, T *__restrict__ y) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -241,13 +244,22 @@ __global__ void k_spmv(int n, int C, const int *slice_ptr, const int *slice_w, c
     const int s = r / C, i = r - s * C;
     const int w = slice_w[s];
     const T sr = scale[r];
-    T acc = sr * x[r];
+    T acc = PRESCALED ? x[r] : sr * x[r];
     for (int k = 0; k < w; ++k) {
         const int at = slice_ptr[s] + k * C + i;
         const int c = col[at];
-        acc = fma(val[at], scale[c] * x[c], acc);
+        acc = fma(val[at], PRESCALED ? x[c] : scale[c] * x[c], acc);
     }
     y[r] = sr * acc;
+}
+
+// u = sd x, the input of the prescaled product
+template <typename T>
+__global__ void k_spmv_prescale(int n, const T *__restrict__ scale, const T *__restrict__ x,
+                                T *__restrict__ u) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n)
+        u[r] = scale[r] * x[r];
 }
 
 // dL/d(diag_extra)_i = -lambda_i x_i (the diagonal enters A as +e_i e_i^T)
