@@ -93,6 +93,44 @@ def test_spmv_parity(pkg, oracle_mod, case, C):
     A.close()
 
 
+def test_spmv_and_solves_share_a_handle(pkg):
+    """The double product passes through one of the handle's work vectors
+    (D^1/2 x, then the product): products between solves leave the solves'
+    results unchanged, solves leave the products unchanged, and coefficient
+    updates reach the float product's copy of the scaling factors."""
+    s = lc.config2(s=24)
+    A = pkg.from_system(s)
+    g = np.random.default_rng(11)
+    x = cuda(g.uniform(-1, 1, s.n))
+    x32 = x.float()
+    b = cuda(s.b)
+    y64 = pkg.ldu_spmv(A, x).clone()
+    y32 = pkg.ldu_spmv(A, x32, precision="fp32").clone()
+    sol = []
+    for _ in range(2):
+        xs, st, it, rr = pkg.pipecg_solve(A, b, tol=1e-10, precision="mixed", deflate=True)
+        assert st == 0
+        sol.append((xs.clone(), it, rr))
+        assert torch.equal(pkg.ldu_spmv(A, x), y64)
+        assert torch.equal(pkg.ldu_spmv(A, x32, precision="fp32"), y32)
+        xp, st, _, _ = pkg.pcg_solve(A, b, tol=1e-10)
+        assert st == 0
+    assert torch.equal(sol[0][0], sol[1][0]) and sol[0][1:] == sol[1][1:]
+    # new values: both products follow them (against the oracle's product)
+    import oracle as om
+    vals = {"diag": 1.5 * s.diag, "upper": 0.7 * s.upper, "lower": 0.7 * s.lower}
+    pkg.ldu_update_values(A, cuda(vals["diag"]), cuda(vals["upper"]), cuda(vals["lower"]))
+    xn = g.uniform(-1, 1, s.n)
+    ref = om.spmv(s, xn, **vals)
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(pkg.ldu_spmv(A, cuda(xn)).cpu().numpy() - ref)) <= 1e-12 * scale
+    xn32 = xn.astype(np.float32)
+    y32n = pkg.ldu_spmv(A, cuda(xn32), precision="fp32").cpu().numpy()
+    ref32 = om.spmv(s, xn32.astype(np.float64), **vals)
+    assert np.max(np.abs(y32n - ref32)) <= 1e-5 * scale
+    A.close()
+
+
 SOLVE_CASES = {
     "c1-16": lambda: lc.config1(s=16),
     "c2-20": lambda: lc.config2(s=20),
