@@ -50,6 +50,15 @@ def test_host_only_calls_without_gpu(libpath):
     lib.ldu_create.restype = ctypes.c_int
     assert lib.ldu_create(ctypes.c_int64(4), ctypes.c_int64(0), None, None, None, None, None,
                           None, None, None) == -1
+    # sizes the 32-bit layout cannot index are refused before any allocation
+    # (the array pointers are only tested for null, never read, on this path)
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(256)
+    assert lib.ldu_create(ctypes.c_int64(1 << 31), ctypes.c_int64(0), None, None, fake, None, None,
+                          None, None, ctypes.byref(h)) == -7
+    assert lib.ldu_create(ctypes.c_int64(8), ctypes.c_int64(1 << 30), fake, fake, fake, fake, fake,
+                          None, None, ctypes.byref(h)) == -7
+    assert h.value is None
     lib.ldu_destroy(None)
 
 
