@@ -132,6 +132,7 @@ def test_spmv_and_solves_share_a_handle(pkg):
 
 
 SOLVE_CASES = {
+    "c1-32": lambda: lc.config1(),   # the 32^3 unit-diffusivity Poisson case at its full size
     "c1-16": lambda: lc.config1(s=16),
     "c2-20": lambda: lc.config2(s=20),
     "c3-16": lambda: lc.config3(s=16),
