@@ -89,15 +89,20 @@ def profiled_traffic(slice_rows=None):
 # Per cell, with f = 2F/n off-diagonal entries per row (actual, padding
 # excluded), float values/indices 4 B, double 8 B; vectors counted once per
 # pass they are read or written, gathers once.
-def bytes_mixed(n, F, iters, reps, col_bytes=4):
+def bytes_mixed(n, F, iters, reps, col_bytes=4, deflated=False):
     """col_bytes: bytes per column index in the float loop (2 when the staged
-    sweep reads 16-bit column offsets)."""
+    sweep reads 16-bit column offsets).  deflated: the constant-vector
+    deflation's three float vectors in every sweep, and its FP64 coarse
+    correction in every replacement."""
     f = 2.0 * F / n
     loop = f * (4 + col_bytes) + 6 * 4 + 6 * 4    # matrix (val32+col) + 6 reads + 6 writes
     rep = (24                                     # fold: xhat rw, xc rw
            + f * 12 + 8 + 8 + 8 + 8 + 4           # FP64 residual: val64+col, xhat, bhat, dg, r out
            + f * 8 + 4 + 4 + 4 + 4                # w = Ar, s = Ap
            + f * 8 + 4 + 4 + 8 + 8 + 4)           # z = As, rescale r, p, read w
+    if deflated:
+        loop += 3 * 4                             # w0, q0, t0 (float) read every sweep
+        rep += 8 + 8 + 5 * 8 + 8 + 4 + 4          # w0 in, r out; xhat, r, w0, q0, dg in, xhat, r out; q0 in
     ends = 8 * 4 + 4 * 4 + 3 * 8                  # prep (b, x0 in; bhat, xhat out; zero 4 float) + unscale
     return n * (iters * loop + reps * rep + ends)
 
@@ -773,12 +778,21 @@ def run_pressure(args, dev, pkg, timed_fn):
     def pcg():
         pkg.pcg_solve(A, b, x, tol=TOL, maxit=50000)
 
+    hbm, _ = peaks()
+    cb = 2 if A.info()["col16"] else 4
     for name, call in (("mixed_deflated", mixed), ("fp64_pcg", pcg)):
         t = timed_fn(call, 2, 1, prep=x.zero_)
         st = A.stats()
-        out[name] = {"s": statistics.median(t), "iters": st["iters"],
+        ts = statistics.median(t)
+        out[name] = {"s": ts, "iters": st["iters"],
                      "replacements": st["replacements"], "relres": st["relres"],
                      "status": st["status"]}
+        # the vectors (0.7 GB in float) no longer fit the L2 here: the
+        # algorithmic bytes are what has to come from HBM
+        alg = (bytes_mixed(s.n, s.nfaces, st["iters"], st["replacements"], cb, deflated=True)
+               if name == "mixed_deflated" else
+               bytes_pcg64(s.n, s.nfaces, st["iters"], st["replacements"]))
+        out[name].update(alg_bytes=alg, alg_gbs=alg / ts / 1e9, frac=alg / ts / 1e9 / hbm)
     out["speedup_mixed_vs_fp64_pcg"] = out["fp64_pcg"]["s"] / out["mixed_deflated"]["s"]
     out["spmv"] = run_spmv(pkg, A, s.nfaces, dev)
     A.close()
